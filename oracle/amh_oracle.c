@@ -249,13 +249,14 @@ static void draw(uint64_t seed, uint32_t chain, uint64_t t, uint32_t stream, uin
   orc_philox4x32_10(ctr, key, out);
 }
 
-/* A uniform on (0,1) from the top 24 bits of a word: ((w>>8)+1/2)/2^24.
- * Exactly representable in binary32 and binary64.                       */
-static double uniform24(uint32_t w) { return ((double)(w >> 8) + 0.5) / 16777216.0; }
+/* A uniform on (0,1) from the top 23 bits of a word: ((w>>9)+1/2)/2^23.
+ * Exactly representable in binary32 and binary64 (24 significant bits),
+ * so a single-precision consumer sees the same value.                   */
+static double uniform23(uint32_t w) { return ((double)(w >> 9) + 0.5) / 8388608.0; }
 
 /* Box-Muller (first branch): z = sqrt(-2 ln u0) cos(2 pi u1). */
 static double box_muller(uint32_t w0, uint32_t w1) {
-  double u0 = uniform24(w0), u1 = uniform24(w1);
+  double u0 = uniform23(w0), u1 = uniform23(w1);
   return sqrt(-2.0 * log(u0)) * cos(2.0 * ORC_PI * u1);
 }
 
@@ -263,7 +264,7 @@ void orc_draw(uint64_t seed, uint32_t chain, uint64_t t, uint32_t stream, uint32
               double* z, double* u) {
   draw(seed, chain, t, stream, out);
   if (z) *z = box_muller(out[0], out[1]);
-  if (u) *u = uniform24(out[2]);
+  if (u) *u = uniform23(out[2]);
 }
 
 /* Wrap to (-pi, pi]. */
