@@ -1,0 +1,385 @@
+"""Benchmark of the AMH hot path on GB300.
+
+One step = one Alternating-MH cycle on every chain (10 local sweeps with
+window d = 8, then 1 global sweep; Alg. 1) along the annealing schedule of
+the L=300, 1024-chain workload (T 2.0 -> 0.05 geometric and sigma 10 -> 4 deg
+over 200k proposals per chain), followed by one gradient evaluation dV/ds
+of every chain's state (the hand-off to L-BFGS).  Metric: MH proposals per
+second over all ranks (weak scaling: each rank owns its own 1024 chains).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "amh_L300_c1024"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+# FP32 lanes per SM on this part (4 sub-partitions x 32) for the ALU peak
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 operations of one pair-term evaluation e(|x_a - x_b|):
+# 3 sub + 3 mul + 2 add (squared distance), 1 sqrt, 1 sub + 1 mul (bin
+# coordinate), 1 sub (fraction), 1 sub + 1 mul + 1 add (interpolation),
+# 1 add (accumulate) = 16
+FLOP_PER_EVAL = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    from paper_2211_03193_gb300 import synth
+    w = dict(synth.WORKLOADS[name])
+    L = w["L"]
+    n = 2 * L
+    w["n"] = n
+    w["total_sweeps"] = w["proposals"] // n
+    w["cycle"] = w["n_local"] + w["n_global"]
+    return w
+
+
+def schedule_for(w, seed):
+    from paper_2211_03193_gb300.sampler import Schedule
+    s0, s1 = w["sigma_deg"] if isinstance(w["sigma_deg"], tuple) else (w["sigma_deg"],) * 2
+    return Schedule(total_sweeps=w["total_sweeps"], n_local=w["n_local"], n_global=w["n_global"],
+                    window=w["window"], T0=w["T0"], T1=w["T1"], sigma0_deg=s0, sigma1_deg=s1,
+                    seed=seed)
+
+
+def pair_evals_per_cycle(w):
+    """Pair-term evaluations one chain performs in one cycle."""
+    L, n, h = w["L"], w["n"], w["window"] // 2
+    glob = 2 * (L ** 3 - L) // 3          # old + new of every straddle pair
+    resync = 2 * (L * (L - 1) // 2)       # entry and exit resync
+    loc = 0
+    for k in range(n):
+        c, p = k // 2, (k + 1) // 2
+        lo, hi = max(0, c - h), min(L - 1, c + h)
+        if lo < p <= hi:
+            loc += 2 * (p - lo) * (hi - p + 1)
+    return w["n_global"] * (glob + resync), w["n_local"] * loc
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, seed, budget_s=12.0):
+    """The FP64 oracle on this host's cores, on a bounded sample of the
+    workload: cycles of the same schedule on as many chains as there are
+    cores (OpenMP over chains)."""
+    import oracle
+    from paper_2211_03193_gb300 import synth
+    oracle.build()
+    prot = synth.make_protein(w["L"], edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    P = oracle.Problem(prot.L, prot.p, prot.edges)
+    cores = oracle.num_threads()
+    S = synth.random_torsions(cores, w["L"], seed=w["start_seed"]).astype(np.float64)
+    sched = schedule_for(w, seed)
+    n = w["n"]
+    props = 0
+    t0 = time.perf_counter()
+    s = 0
+    while True:
+        mode, T, sigma = sched.params(s)
+        S, _ = P.run_chains(S, mode, w["window"], T, sigma, s * n, n, seed, 0)
+        props += cores * n
+        s += 1
+        if time.perf_counter() - t0 > budget_s and s % w["cycle"] == 0:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": props / dt, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d chains x %d sweeps (%d cycles of %d local + %d global, L=%d) of the "
+                      "same schedule, FP64, OpenMP over chains" % (
+                          cores, s, s // w["cycle"], w["n_local"], w["n_global"], w["L"]),
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    n = w["n"]
+    # each step is a bounded sample: one cycle on `cores` chains
+    import oracle
+    from paper_2211_03193_gb300 import synth
+    oracle.build()
+    prot = synth.make_protein(w["L"], edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    P = oracle.Problem(prot.L, prot.p, prot.edges)
+    cores = oracle.num_threads()
+    S = synth.random_torsions(cores, w["L"], seed=w["start_seed"]).astype(np.float64)
+    sched = schedule_for(w, 1)
+    s = 0
+
+    def one_step():
+        nonlocal S, s
+        for _ in range(w["cycle"]):
+            mode, T, sigma = sched.params(s)
+            S, _ = P.run_chains(S, mode, w["window"], T, sigma, s * n, n, 1, 0)
+            s += 1
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = time.perf_counter() - t0
+    props = args.steps * w["cycle"] * n * cores
+    val = props / dt
+    out = {"metric": "MH proposals/s", "value": val, "unit": "proposals/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload + " (oracle sample: %d chains per step)" % cores,
+                      "L": w["L"], "chains_per_step": cores, "schedule": "10 local (d=8) : 1 global"},
+           "cpu_baseline": {"value": val, "unit": "proposals/s", "cores": cores, "kind": "oracle",
+                            "sample": "%d chains x 1 cycle per step" % cores},
+           "e2e": {"value": val, "unit": "proposals/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2211_03193_gb300 import build as b
+    b.build()
+    from paper_2211_03193_gb300 import _amh, synth
+    from paper_2211_03193_gb300.sampler import Sampler
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = workload(args.workload)
+    L, n, chains = w["L"], w["n"], w["chains"]
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    tors = synth.random_torsions(chains, L, seed=w["start_seed"] + 1000 * rank)
+    stream = torch.cuda.Stream()
+    samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream)
+    C, thr = samp.launch_config()
+    sched = schedule_for(w, seed=1 + rank)
+    cyc = w["cycle"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    theta_dev = torch.empty((chains, n), dtype=torch.float32, device="cuda")
+    E_dev = torch.empty(chains, dtype=torch.float64, device="cuda")
+    G_dev = torch.empty((chains, n), dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    sweep_idx = [0]
+
+    def cycle(glob_events=None):
+        for j in range(cyc):
+            s = sweep_idx[0] % w["total_sweeps"]
+            mode, T, sigma = sched.params(s)
+            if mode == _amh.AMH_GLOBAL and glob_events is not None:
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                _amh.amh_sweeps(samp.ctx, mode, w["window"], T, sigma, 1, sched.seed, None)
+                e1.record(stream)
+                glob_events.append((e0, e1))
+            else:
+                _amh.amh_sweeps(samp.ctx, mode, w["window"], T, sigma, 1, sched.seed, None)
+            sweep_idx[0] += 1
+        # hand-off: gradient of every chain's current state
+        _amh.amh_get_state(samp.ctx, theta_dev, None, None, None)
+        _amh.amh_grad(samp.ctx, 0, theta_dev, chains, E_dev, G_dev)
+
+    # the schedule's global sweep is the cycle's last sweep; align to a cycle
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            cycle()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = []
+    glob_ev = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(len(step_ms)))  # evict L2 between timed steps
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                cycle(glob_ev)
+                e1.record(stream)
+            step_ms.append((e0, e1))
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b_) for a, b_ in step_ms)
+    glob_ms = [a.elapsed_time(b_) for a, b_ in glob_ev]
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    props_step = cyc * n * chains
+    value = props_step * args.steps * world / (total_ms / 1000.0)
+    ev_glob, ev_loc = pair_evals_per_cycle(w)
+    evals_step = (ev_glob + ev_loc) * chains
+
+    # e2e through the public API with host buffers: per step, upload the
+    # chains' torsions from pinned memory, run the cycle, read back torsions
+    # and energies.
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(tors.copy()).pin_memory()
+        h_out = torch.empty((chains, n), dtype=torch.float32).pin_memory()
+        h_E = torch.empty(chains, dtype=torch.float64).pin_memory()
+        h_bE = torch.empty(chains, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                _amh.amh_set_state(samp.ctx, h_in)
+                cycle()
+                _amh.amh_get_state(samp.ctx, h_out, h_E, h_bE, None)
+                h_in.copy_(h_out)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": props_step * args.steps * world / dt, "unit": "proposals/s",
+               "h2d_bytes_per_step": int(h_in.numel() * 4),
+               "d2h_bytes_per_step": int(h_out.numel() * 4 + 16 * chains),
+               "timing": "host wall clock around set_state + cycle + get_state, synchronised"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    pk, src = peaks()
+    clocks = clk.summary()
+    g_ms = float(np.mean(glob_ms)) if glob_ms else float("nan")
+    L3 = 2 * (L ** 3 - L) // 3 + 2 * (L * (L - 1) // 2)
+    evals_glob_launch = L3 * chains
+    achieved = evals_glob_launch * FLOP_PER_EVAL / (g_ms / 1000.0) / 1e12
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": achieved / peak_tf, "traffic": None,
+            "kernel": "global_kernel<float,%d> (global sweep, %d threads/CTA)" % (C, thr),
+            "launch_ms": g_ms, "pair_evals_per_launch": evals_glob_launch,
+            "flop_per_eval": FLOP_PER_EVAL,
+            "peak_basis": "%d SMs x %d FP32 lanes x 2 (FMA) x %.0f MHz (%s max clock)" % (
+                sm_count, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src)}
+    out = {"metric": "MH proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "L": L, "chains_per_gpu": chains, "bins": w["bins"], "schedule": "10 local (d=8) : 1 global per step, "
+                      "T 2.0->0.05, sigma 10->4 deg over %d sweeps" % w["total_sweeps"],
+                      "proposals_per_step_per_gpu": props_step, "l2": "flushed between steps "
+                      "(256 MB write); table 6.6 MB is L2-resident within a step",
+                      "chains_per_cta": C, "threads_per_cta": thr,
+                      "parallelism": "independent chains per GPU (replicas)"},
+           "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
+           "roofline": roof, "gpu_launches": args.steps * (cyc + 1),
+           "clocks": clocks, "e2e": e2e}
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w, seed=1)
+    print(json.dumps(out))
+    samp.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * amh.h -- C ABI of the GB300 (sm_103a) Alternating Metropolis-Hastings
+ * library: many independent MCMC chains over backbone torsions, scored by
+ * a distogram energy (Ghantasala, Jaiswal & Datta, arXiv 2211.03193).
+ *
+ * Problem statement (Sec. 2.1, Sec. 2.3): the state of one chain is the
+ * torsion vector s of n = 2L angles for a protein of L residues,
+ * s[2i] = phi_i and s[2i+1] = psi_i (radians, wrapped to (-pi, pi]);
+ * omega is fixed at 180 deg.  x = G(s) are the C-beta coordinates built by
+ * NeRF with ideal geometry (N-CA 1.458, CA-C 1.525, C-N 1.329 A; N-CA-C
+ * 111.2, CA-C-N 116.2, C-N-CA 121.7 deg; virtual C-beta 1.52 A, C-CA-CB
+ * 109.5 deg, improper N-C-CA-CB +122.6 deg).  The energy is Eq. 5 over
+ * unordered residue pairs a<b: V(x) = sum -ln p_ab(|x_a - x_b|), with -ln p
+ * interpolated linearly between bin centres and flat beyond the first and
+ * last centres; the window energy V_local(x,k,d) of Eq. 6 sums the pairs
+ * inside residues floor(k/2) -+ floor(d/2).
+ *
+ * Conventions for every call:
+ *  - Every call returns an amh_status; nothing throws across the ABI.
+ *  - A context owns all of its device memory; the caller owns every buffer
+ *    it passes in.  Inputs are copied; output buffers are written.
+ *  - "host or device" pointers are told apart with cudaPointerGetAttributes;
+ *    device pointers must be on the context's device.
+ *  - All work is issued on the context's stream (amh_options.stream).
+ *    Calls whose output is host memory synchronise that stream; calls
+ *    whose outputs are device memory (or NULL) return without waiting.
+ *  - A CUDA error makes the context sticky-broken: that call returns
+ *    AMH_ECUDA and every later call AMH_ESTATE until amh_destroy.
+ *  - A context is used from one host thread at a time.
+ */
+#ifndef AMH_H
+#define AMH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amh_ctx amh_ctx;
+
+typedef enum {
+  AMH_OK = 0,
+  AMH_EINVAL = 1,   /* bad argument; nothing was done */
+  AMH_ENOMEM = 2,   /* device allocation failed */
+  AMH_ECUDA = 3,    /* CUDA runtime error (context is now broken) */
+  AMH_ETIMEOUT = 4, /* a bounded device wait gave up (reserved) */
+  AMH_ESTATE = 5    /* context broken by an earlier error, or NULL */
+} amh_status;
+
+typedef enum {
+  AMH_LOCAL = 0,  /* localized MH: Eqs. 4a-b with V_local of Eq. 6 */
+  AMH_GLOBAL = 1  /* traditional MH: Eqs. 1-3 with V of Eq. 5 */
+} amh_mode;
+
+typedef struct {
+  int precision;           /* 32 (default): FP32 coordinates and pair terms,
+                              FP64 running energy; 64: FP64 throughout. */
+  int resync_every;        /* global sweeps rebuild G(s) and recompute V in
+                              FP64 every this many proposals (default 1000). */
+  int chains_per_cta;      /* chains that share one CTA in global sweeps:
+                              0 = autotuned at first use, else 1, 2, 4 or 8. */
+  int threads_per_cta;     /* 0 = default (256 for global sweeps). */
+  int trace_chains;        /* record every proposal of chains [0, trace_chains) */
+  long long trace_capacity;/* records kept per traced chain (visit order) */
+  int lattice_K;           /* test mode: 0 = off; K > 0 snaps proposals to a
+                              K-point lattice, s' = q round((s + sigma z)/q),
+                              q = 2 pi / K (symmetric proposal). */
+  int table_is_neglog;     /* 0: table holds p; 1: table already holds -ln p */
+  void* stream;            /* cudaStream_t; NULL = the legacy default stream */
+} amh_options;
+
+/* One proposal record (traced chains only), 32 bytes. */
+typedef struct {
+  int k;             /* torsion index */
+  int accept;        /* 1 if accepted */
+  double theta_new;  /* proposed value s'_k (radians, wrapped) */
+  double lnu;        /* ln u of the accept uniform */
+  double dE;         /* Delta V (global) or Delta V_local (local) used */
+} amh_trace_rec;
+
+/* Fill *opt with the defaults listed above. */
+void amh_options_default(amh_options* opt);
+
+/*
+ * amh_init -- create a context holding n_proteins problems and their chains
+ * (Alg. 1 "input": the initial state s^0 of every chain; Eq. 5's
+ * distogram P(d | S, MSA(S)) per protein).
+ *   L[p]                residues of protein p (2 <= L <= 4096)
+ *   chains_per_protein  chains of protein p (>= 1); chain ids run protein
+ *                       by protein: protein 0's chains first.
+ *   torsions            host, float32, the chains' starting s concatenated
+ *                       chain by chain: sum_p chains[p] * 2 L[p] values.
+ *   table               host, float64, per protein in order, rows
+ *                       r(a,b) = a L - a(a+1)/2 + (b-a-1) for a<b, each row
+ *                       B values in ascending distance order: p (or -ln p
+ *                       if table_is_neglog).  p is floored at 1e-300.
+ *   edges               host, float64 [B+1] ascending, shared by all
+ *                       proteins; edges[B] may be +INFINITY (open last bin,
+ *                       centre = edges[B-1] + (edges[B-1]-edges[B-2])/2).
+ *                       Bin centres must be evenly spaced (relative 1e-9),
+ *                       else AMH_EINVAL.
+ *   B                   bins, 2 <= B <= 256.
+ *   opt                 options (NULL = defaults).
+ * Computes G(s) and V for every chain; best energy = starting energy.
+ */
+amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chains_per_protein,
+                    const float* torsions, const double* table, const double* edges, int B,
+                    const amh_options* opt);
+
+/*
+ * amh_energy -- V(G(s)) of Eq. 5 for every chain's current state: FP32 (or
+ * FP64) pair terms summed in FP64.  E_out: [total chains] doubles, host or
+ * device.
+ */
+amh_status amh_energy(amh_ctx* ctx, double* E_out);
+
+/*
+ * amh_sweep -- run `steps` Metropolis proposals on every chain (Alg. 1 inner
+ * loops).  Each chain keeps a proposal counter t (0 after amh_init); the
+ * proposal with index t perturbs torsion k = t mod n by sigma_rad * z
+ * (Eq. 2), z and the accept uniform u drawn from Philox4x32-10 with key
+ * `seed` and counter (chain id, t low word, t high word, 0); Box-Muller
+ * z = sqrt(-2 ln u0) cos(2 pi u1) with u_i = ((w_i >> 9) + 1/2) / 2^23.
+ * Accept iff ln u < -dE / T (Eq. 1 with P = exp(-V/T)).
+ *   mode AMH_GLOBAL  dE = V(G(s')) - V(G(s)), k visited in order; window
+ *                    ignored.
+ *   mode AMH_LOCAL   dE = V_local(G(s'),k,d) - V_local(G(s),k,d), d = window
+ *                    (0 <= d <= 64); whole sweeps only: t and steps must be
+ *                    multiples of n for every protein, else AMH_EINVAL.
+ *                    Within a sweep, torsions are visited by colour
+ *                    (k mod max(4 floor(d/2), 1) ascending, then k
+ *                    ascending); same-colour windows touch disjoint torsions
+ *                    and are evaluated concurrently.
+ *   accepted_out     NULL, or [total chains] long long (host or device):
+ *                    accepted proposals of this call per chain.
+ * Global sweeps end with an FP64 resync and update each chain's best state.
+ * Split calls equal one long call (the counter continues).
+ */
+amh_status amh_sweep(amh_ctx* ctx, int mode, int window, double T, double sigma_rad,
+                     long long steps, unsigned long long seed, long long* accepted_out);
+
+/*
+ * amh_sweeps -- like amh_sweep but in whole sweeps: every chain of protein
+ * p runs nsweeps * 2 L[p] proposals (for contexts holding proteins of
+ * different lengths).
+ */
+amh_status amh_sweeps(amh_ctx* ctx, int mode, int window, double T, double sigma_rad,
+                      long long nsweeps, unsigned long long seed, long long* accepted_out);
+
+/*
+ * amh_grad -- energy and its gradient for a batch of torsion vectors of one
+ * protein of the context (the dV/ds the abstract's L-BFGS pairing needs).
+ *   theta       device, [batch][2 L] (float32, or float64 if precision 64)
+ *   E_out       device, [batch] doubles: V(G(theta))
+ *   dE_dtheta   device, [batch][2 L], same type as theta
+ * dV/ds_k = u_k . (M_p - o_k x G_p): G_p and M_p are suffix sums over C-beta
+ * b >= p(k) of the pair-force sum g_b and of x_b x g_b; u_k the unit bond
+ * axis and o_k its first atom.  Kinks of the piecewise-linear term take the
+ * slope of the segment to their right.
+ */
+amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, double* E_out,
+                    void* dE_dtheta);
+
+/*
+ * amh_get_state -- copy out the chains' state; any pointer may be NULL.
+ *   torsions_out, best_torsions  [sum chains * 2 L] float32 (host or device)
+ *   E_out      energy after the last global sweep / energy call [chains]
+ *   best_E     lowest energy seen at a global-sweep end [chains]
+ */
+amh_status amh_get_state(amh_ctx* ctx, float* torsions_out, double* E_out, double* best_E,
+                         float* best_torsions);
+
+/* amh_set_state -- replace every chain's torsions (host or device, float32,
+ * layout as in amh_init) and recompute V.  Counters and best are kept.     */
+amh_status amh_set_state(amh_ctx* ctx, const float* torsions);
+
+/* amh_noisy_restart -- s_k += sd_rad * z for every torsion of every chain,
+ * z from Philox counter (chain, k, 0, 1) under key `seed`, then wrap; V is
+ * recomputed (the noisy-restart baseline of Sec. 3).                       */
+amh_status amh_noisy_restart(amh_ctx* ctx, double sd_rad, unsigned long long seed);
+
+/* amh_get_trace -- copy the trace of chain `chain` (< trace_chains):
+ * records [0, min(count, trace_capacity)) in visit order into `out` (host),
+ * *count set to the records written so far.                              */
+amh_status amh_get_trace(amh_ctx* ctx, int chain, amh_trace_rec* out, long long* count);
+
+/* amh_counter -- the proposal counter t of chain `chain`. */
+amh_status amh_counter(amh_ctx* ctx, int chain, long long* t);
+
+/*
+ * amh_philox -- the sampler's random stream, for checking: for
+ * t = t0 .. t0+count-1 writes Philox4x32-10(key seed; counter (chain,
+ * t_lo, t_hi, stream)) to words_out[count][4] and, for stream 0, the FP32
+ * Box-Muller normal and accept uniform to z_out/u_out (any may be NULL).
+ * All output pointers are host memory.  Runs on the current device.
+ */
+amh_status amh_philox(unsigned long long seed, unsigned chain, unsigned long long t0,
+                      unsigned stream, long long count, unsigned* words_out, float* z_out,
+                      float* u_out);
+
+/* Text of the last error of ctx (or of the last context-free call). */
+const char* amh_last_error(const amh_ctx* ctx);
+
+/* Chains per CTA and threads per CTA the global sweeps use (after tuning). */
+amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta);
+
+/* Free everything the context owns.  NULL is ignored. */
+void amh_destroy(amh_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMH_H */

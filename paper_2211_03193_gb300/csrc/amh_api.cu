@@ -1,0 +1,881 @@
+// amh_api.cu -- the C ABI declared in include/amh.h: argument checks, device
+// memory, launch configuration (with a small autotuner) and the calls that
+// run the kernels of amh_global.cu, amh_local.cu and amh_misc.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amh.h"
+#include "amh_internal.h"
+
+using namespace amh;
+
+struct amh_ctx {
+  int device = 0;
+  int precision = 32;
+  amh_options opt;
+  cudaStream_t stream = nullptr;
+  int nprot = 0;
+  std::vector<int> L, nch;
+  std::vector<ProteinDev> prot_h;
+  std::vector<long long> t_host;  // per protein proposal counter (mirror)
+  int total_chains = 0;
+  long long tors_total = 0;
+  int Lmax = 0, nmax = 0;
+  int B = 0, Bp = 0;
+  double c0 = 0, w = 0;
+  long long rows_total = 0;
+  // device memory
+  void* table = nullptr;
+  void* theta = nullptr;
+  void* best_theta = nullptr;
+  float* f32buf = nullptr;  // FP32 staging for precision-64 conversions
+  long long* tcount = nullptr;
+  double* E_cur = nullptr;
+  double* best_E = nullptr;
+  long long* acc = nullptr;
+  ProteinDev* prot_d = nullptr;
+  int* chain_prot_d = nullptr;
+  GroupDev* ggroups_d = nullptr;  // global groups for the chosen C
+  int nggroups = 0;
+  GroupDev* lgroups_d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // Gc = 1..32
+  int nlgroups[6] = {0, 0, 0, 0, 0, 0};
+  int* queue = nullptr;
+  int* err = nullptr;
+  TraceRec* trace = nullptr;
+  long long* trace_count = nullptr;
+  // launch configuration
+  int C = 8, threads = 256, grid_global = 1;
+  int sm_count = 1;
+  size_t smem_optin = 0;
+  std::string msg;
+  bool broken = false;
+};
+
+namespace {
+
+thread_local std::string g_free_error;
+
+amh_status set_err(amh_ctx* ctx, amh_status st, const std::string& m) {
+  if (ctx) {
+    ctx->msg = m;
+    if (st == AMH_ECUDA) ctx->broken = true;
+  } else {
+    g_free_error = m;
+  }
+  return st;
+}
+
+amh_status cuda_fail(amh_ctx* ctx, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    if (ctx) ctx->msg = m;
+    return AMH_ENOMEM;
+  }
+  return set_err(ctx, AMH_ECUDA, m);
+}
+
+#define CK(ctx, call)                                         \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <class R>
+Geom<R> make_geom() {
+  const double d2r = 3.14159265358979323846 / 180.0;
+  const double bNCA = 1.458, bCAC = 1.525, bCN = 1.329, bCACB = 1.52;
+  const double aNCAC = 111.2 * d2r, aCACN = 116.2 * d2r, aCNCA = 121.7 * d2r;
+  const double aCCACB = 109.5 * d2r, tCB = 122.6 * d2r;
+  Geom<R> g;
+  g.bNCA = (R)bNCA;
+  g.bCAC = (R)bCAC;
+  g.cosNCAC = (R)std::cos(aNCAC);
+  g.sinNCAC = (R)std::sin(aNCAC);
+  g.pN_c = (R)(-bCN * std::cos(aCACN));
+  g.pN_s = (R)(bCN * std::sin(aCACN));
+  g.pCA_c = (R)(-bNCA * std::cos(aCNCA));
+  g.pCA_s = (R)(bNCA * std::sin(aCNCA));
+  g.pC_c = (R)(-bCAC * std::cos(aNCAC));
+  g.pC_s = (R)(bCAC * std::sin(aNCAC));
+  g.pCB_c = (R)(-bCACB * std::cos(aCCACB));
+  g.pCB_s = (R)(bCACB * std::sin(aCCACB));
+  g.cbT_c = (R)std::cos(tCB);
+  g.cbT_s = (R)std::sin(tCB);
+  return g;
+}
+
+template <class R>
+Tab<R> make_tab(const amh_ctx* ctx) {
+  Tab<R> t;
+  t.E = (const R*)ctx->table;
+  t.inv_w = (R)(1.0 / ctx->w);
+  t.off = (R)(-ctx->c0 / ctx->w);
+  t.umax = (R)(ctx->B - 1);
+  t.Bp = ctx->Bp;
+  return t;
+}
+
+template <class R>
+SweepArgs<R> make_args(amh_ctx* ctx) {
+  SweepArgs<R> a;
+  memset(&a, 0, sizeof(a));
+  a.prot = ctx->prot_d;
+  a.groups = ctx->ggroups_d;
+  a.ngroups = ctx->nggroups;
+  a.queue = ctx->queue;
+  a.theta = (R*)ctx->theta;
+  a.best_theta = (R*)ctx->best_theta;
+  a.tcount = ctx->tcount;
+  a.E_cur = ctx->E_cur;
+  a.best_E = ctx->best_E;
+  a.acc_out = ctx->acc;
+  a.tab = make_tab<R>(ctx);
+  a.geom = make_geom<R>();
+  a.resync_every = ctx->opt.resync_every;
+  a.lattice_K = ctx->opt.lattice_K;
+  a.Lmax = ctx->Lmax;
+  a.nmax = ctx->nmax;
+  a.trace = ctx->trace;
+  a.trace_chains = ctx->trace ? ctx->opt.trace_chains : 0;
+  a.trace_cap = ctx->opt.trace_capacity;
+  a.trace_count = ctx->trace_count;
+  a.err = ctx->err;
+  return a;
+}
+
+// ---- dispatch over (precision, C) ------------------------------------------
+template <class R>
+size_t gsmem(int C, int Lmax, int nmax, int threads) {
+  switch (C) {
+    case 1: return global_smem_bytes<R, 1>(Lmax, nmax, threads);
+    case 2: return global_smem_bytes<R, 2>(Lmax, nmax, threads);
+    case 4: return global_smem_bytes<R, 4>(Lmax, nmax, threads);
+    default: return global_smem_bytes<R, 8>(Lmax, nmax, threads);
+  }
+}
+template <>
+size_t gsmem<double>(int C, int Lmax, int nmax, int threads) {
+  switch (C) {
+    case 1: return global_smem_bytes<double, 1>(Lmax, nmax, threads);
+    case 2: return global_smem_bytes<double, 2>(Lmax, nmax, threads);
+    default: return global_smem_bytes<double, 4>(Lmax, nmax, threads);
+  }
+}
+
+template <class R>
+cudaError_t gset(int C, size_t bytes) {
+  switch (C) {
+    case 1: return global_set_smem<R, 1>(bytes);
+    case 2: return global_set_smem<R, 2>(bytes);
+    case 4: return global_set_smem<R, 4>(bytes);
+    default: return global_set_smem<R, 8>(bytes);
+  }
+}
+template <>
+cudaError_t gset<double>(int C, size_t bytes) {
+  switch (C) {
+    case 1: return global_set_smem<double, 1>(bytes);
+    case 2: return global_set_smem<double, 2>(bytes);
+    default: return global_set_smem<double, 4>(bytes);
+  }
+}
+
+template <class R>
+cudaError_t gocc(int C, int threads, size_t sm, int* per_sm) {
+  switch (C) {
+    case 1: return global_occupancy<R, 1>(threads, sm, per_sm);
+    case 2: return global_occupancy<R, 2>(threads, sm, per_sm);
+    case 4: return global_occupancy<R, 4>(threads, sm, per_sm);
+    default: return global_occupancy<R, 8>(threads, sm, per_sm);
+  }
+}
+template <>
+cudaError_t gocc<double>(int C, int threads, size_t sm, int* per_sm) {
+  switch (C) {
+    case 1: return global_occupancy<double, 1>(threads, sm, per_sm);
+    case 2: return global_occupancy<double, 2>(threads, sm, per_sm);
+    default: return global_occupancy<double, 4>(threads, sm, per_sm);
+  }
+}
+
+template <class R>
+cudaError_t glaunch(bool energy, int C, const SweepArgs<R>& a, int threads, int grid,
+                    cudaStream_t st) {
+  switch (C) {
+    case 1: return energy ? launch_energy<R, 1>(a, threads, grid, st) : launch_global<R, 1>(a, threads, grid, st);
+    case 2: return energy ? launch_energy<R, 2>(a, threads, grid, st) : launch_global<R, 2>(a, threads, grid, st);
+    case 4: return energy ? launch_energy<R, 4>(a, threads, grid, st) : launch_global<R, 4>(a, threads, grid, st);
+    default: return energy ? launch_energy<R, 8>(a, threads, grid, st) : launch_global<R, 8>(a, threads, grid, st);
+  }
+}
+template <>
+cudaError_t glaunch<double>(bool energy, int C, const SweepArgs<double>& a, int threads, int grid,
+                            cudaStream_t st) {
+  switch (C) {
+    case 1: return energy ? launch_energy<double, 1>(a, threads, grid, st) : launch_global<double, 1>(a, threads, grid, st);
+    case 2: return energy ? launch_energy<double, 2>(a, threads, grid, st) : launch_global<double, 2>(a, threads, grid, st);
+    default: return energy ? launch_energy<double, 4>(a, threads, grid, st) : launch_global<double, 4>(a, threads, grid, st);
+  }
+}
+
+int max_C(int precision) { return precision == 64 ? 4 : 8; }
+
+// Group chains of each protein C at a time; order groups by decreasing cost
+// (a global sweep of a chain costs ~ L^3) so the persistent CTAs that pull
+// from the queue finish together.
+std::vector<GroupDev> make_groups(const amh_ctx* ctx, int C) {
+  std::vector<GroupDev> g;
+  for (int p = 0; p < ctx->nprot; ++p) {
+    for (int c = 0; c < ctx->nch[p]; c += C) {
+      GroupDev d;
+      d.protein = p;
+      d.chain0 = ctx->prot_h[p].chain0 + c;
+      d.nchains = std::min(C, ctx->nch[p] - c);
+      d.pad = 0;
+      g.push_back(d);
+    }
+  }
+  std::stable_sort(g.begin(), g.end(), [&](const GroupDev& a, const GroupDev& b) {
+    return ctx->L[a.protein] > ctx->L[b.protein];
+  });
+  return g;
+}
+
+amh_status upload_groups(amh_ctx* ctx, const std::vector<GroupDev>& g, GroupDev** dst, int* n) {
+  if (*dst) {
+    cudaFree(*dst);
+    *dst = nullptr;
+  }
+  CK(ctx, cudaMalloc(dst, sizeof(GroupDev) * std::max<size_t>(1, g.size())));
+  CK(ctx, cudaMemcpy(*dst, g.data(), sizeof(GroupDev) * g.size(), cudaMemcpyHostToDevice));
+  *n = (int)g.size();
+  return AMH_OK;
+}
+
+template <class R>
+amh_status configure_global(amh_ctx* ctx, int C, int threads) {
+  const size_t sm = gsmem<R>(C, ctx->Lmax, ctx->nmax, threads);
+  if (sm > ctx->smem_optin) return set_err(ctx, AMH_EINVAL, "shared memory for this C does not fit");
+  amh_status st = upload_groups(ctx, make_groups(ctx, C), &ctx->ggroups_d, &ctx->nggroups);
+  if (st) return st;
+  ctx->C = C;
+  ctx->threads = threads;
+  // persistent grid: as many CTAs as are resident at once, at most one per group
+  int per_sm = 1;
+  CK(ctx, gocc<R>(C, threads, sm, &per_sm));
+  ctx->grid_global = std::max(1, std::min(ctx->nggroups, ctx->sm_count * std::max(per_sm, 1)));
+  return AMH_OK;
+}
+
+template <class R>
+amh_status run_energy(amh_ctx* ctx) {
+  SweepArgs<R> a = make_args<R>(ctx);
+  CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
+  CK(ctx, glaunch<R>(true, ctx->C, a, ctx->threads, ctx->grid_global, ctx->stream));
+  return AMH_OK;
+}
+
+template <class R>
+amh_status run_best(amh_ctx* ctx, int init) {
+  CK(ctx, launch_best<R>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains, ctx->nmax,
+                         (const R*)ctx->theta, (R*)ctx->best_theta, ctx->E_cur, ctx->best_E, init,
+                         ctx->stream));
+  return AMH_OK;
+}
+
+amh_status check_err_flag(amh_ctx* ctx) {
+  int h = 0;
+  CK(ctx, cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h) return set_err(ctx, AMH_ECUDA, "device reported a non-finite energy");
+  return AMH_OK;
+}
+
+// Time a few global proposals around the middle of the chain for each
+// candidate launch shape on scratch copies of the state; keep the fastest.
+template <class R>
+amh_status autotune(amh_ctx* ctx) {
+  const int cand_C[4] = {1, 2, 4, 8};
+  const int cand_T[2] = {128, 256};
+  long long* t_scr = nullptr;
+  R* th_scr = nullptr;
+  R* bt_scr = nullptr;
+  double *e_scr = nullptr, *be_scr = nullptr;
+  const size_t tb = sizeof(R) * (size_t)ctx->tors_total;
+  CK(ctx, cudaMalloc(&t_scr, sizeof(long long) * ctx->total_chains));
+  CK(ctx, cudaMalloc(&th_scr, tb));
+  CK(ctx, cudaMalloc(&bt_scr, tb));
+  CK(ctx, cudaMalloc(&e_scr, sizeof(double) * ctx->total_chains));
+  CK(ctx, cudaMalloc(&be_scr, sizeof(double) * ctx->total_chains));
+  cudaEvent_t e0, e1;
+  CK(ctx, cudaEventCreate(&e0));
+  CK(ctx, cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int bestC = 0, bestT = 256;
+  const long long steps = 64;
+  std::vector<long long> tstart(ctx->total_chains);
+  for (int p = 0; p < ctx->nprot; ++p)
+    for (int c = 0; c < ctx->nch[p]; ++c)
+      tstart[ctx->prot_h[p].chain0 + c] = std::max(0, ctx->prot_h[p].n / 2 - 32);
+  for (int C : cand_C) {
+    if (C > max_C(ctx->precision)) continue;
+    for (int T : cand_T) {
+      if (gsmem<R>(C, ctx->Lmax, ctx->nmax, T) > ctx->smem_optin) continue;
+      amh_status st = configure_global<R>(ctx, C, T);
+      if (st) return st;
+      float ms_sum = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        CK(ctx, cudaMemcpyAsync(th_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(bt_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(t_scr, tstart.data(), sizeof(long long) * ctx->total_chains,
+                                cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemsetAsync(be_scr, 0x7f, sizeof(double) * ctx->total_chains, ctx->stream));
+        SweepArgs<R> a = make_args<R>(ctx);
+        a.theta = th_scr;
+        a.best_theta = bt_scr;
+        a.tcount = t_scr;
+        a.E_cur = e_scr;
+        a.best_E = be_scr;
+        a.acc_out = nullptr;
+        a.trace_chains = 0;
+        a.trace_count = nullptr;
+        a.T = 1.0;
+        a.sigma = (R)0.1;
+        a.seed = 12345;
+        a.steps = steps;
+        a.resync_every = 1 << 30;
+        CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
+        CK(ctx, cudaEventRecord(e0, ctx->stream));
+        CK(ctx, glaunch<R>(false, C, a, T, ctx->grid_global, ctx->stream));
+        CK(ctx, cudaEventRecord(e1, ctx->stream));
+        CK(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (rep) ms_sum += ms;  // first run warms up
+      }
+      if (ms_sum < best_ms) {
+        best_ms = ms_sum;
+        bestC = C;
+        bestT = T;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(t_scr);
+  cudaFree(th_scr);
+  cudaFree(bt_scr);
+  cudaFree(e_scr);
+  cudaFree(be_scr);
+  if (!bestC) return set_err(ctx, AMH_EINVAL, "no launch shape fits in shared memory");
+  return configure_global<R>(ctx, bestC, bestT);
+}
+
+template <class R>
+amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
+  // table: p (or -ln p) -> padded R rows, via a temporary FP64 copy
+  double* tmp = nullptr;
+  const size_t tbytes = sizeof(double) * (size_t)ctx->rows_total * ctx->B;
+  CK(ctx, cudaMalloc(&ctx->table, sizeof(R) * (size_t)ctx->rows_total * ctx->Bp + 64));
+  CK(ctx, cudaMalloc(&tmp, std::max<size_t>(tbytes, 8)));
+  CK(ctx, cudaMemcpy(tmp, table, tbytes, cudaMemcpyHostToDevice));
+  CK(ctx, launch_prep_table<R>(tmp, ctx->rows_total, ctx->B, ctx->Bp, ctx->opt.table_is_neglog,
+                               (R*)ctx->table, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  cudaFree(tmp);
+  // state
+  const size_t tb = sizeof(R) * (size_t)ctx->tors_total;
+  CK(ctx, cudaMalloc(&ctx->theta, tb));
+  CK(ctx, cudaMalloc(&ctx->best_theta, tb));
+  CK(ctx, cudaMalloc(&ctx->f32buf, sizeof(float) * (size_t)ctx->tors_total));
+  CK(ctx, cudaMemcpy(ctx->f32buf, torsions, sizeof(float) * (size_t)ctx->tors_total,
+                     cudaMemcpyHostToDevice));
+  CK(ctx, launch_convert_in<R>(ctx->f32buf, (R*)ctx->theta, ctx->tors_total, ctx->stream));
+  // kernels may use all of the opt-in shared memory
+  for (int C = 1; C <= max_C(ctx->precision); C *= 2) CK(ctx, gset<R>(C, ctx->smem_optin));
+  CK(ctx, local_set_smem<R>(ctx->smem_optin));
+  // launch shape
+  amh_status st;
+  if (ctx->opt.chains_per_cta == 0) {
+    st = autotune<R>(ctx);
+  } else {
+    const int T = ctx->opt.threads_per_cta ? ctx->opt.threads_per_cta : 256;
+    st = configure_global<R>(ctx, ctx->opt.chains_per_cta, T);
+  }
+  if (st) return st;
+  // local groups for every chains-per-CTA option
+  for (int q = 0; q < 6; ++q) {
+    st = upload_groups(ctx, make_groups(ctx, 1 << q), &ctx->lgroups_d[q], &ctx->nlgroups[q]);
+    if (st) return st;
+  }
+  st = run_energy<R>(ctx);
+  if (st) return st;
+  st = run_best<R>(ctx, 1);
+  if (st) return st;
+  return check_err_flag(ctx);
+}
+
+template <class R>
+amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma, long long steps,
+                      int are_sweeps, unsigned long long seed) {
+  SweepArgs<R> a = make_args<R>(ctx);
+  a.T = T;
+  a.sigma = (R)sigma;
+  a.seed = seed;
+  a.steps = steps;
+  a.steps_are_sweeps = are_sweeps;
+  a.window = window;
+  CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
+  if (mode == AMH_GLOBAL) {
+    CK(ctx, glaunch<R>(false, ctx->C, a, ctx->threads, ctx->grid_global, ctx->stream));
+  } else {
+    const int h = window / 2;
+    const int ncol = std::max(4 * h, 1);
+    const int cnt = (ctx->nmax + ncol - 1) / ncol;
+    int q = 0;
+    while (q < 5 && (2 << q) * cnt <= 256) ++q;  // Gc = 2^q with Gc * cnt <= 256
+    const int Gc = 1 << q;
+    int threads = 256;
+    size_t sm = local_smem_bytes<R>(ctx->nmax, Gc, threads, window);
+    while (sm > ctx->smem_optin && threads > 32) {
+      threads /= 2;
+      sm = local_smem_bytes<R>(ctx->nmax, Gc, threads, window);
+    }
+    if (sm > ctx->smem_optin) return set_err(ctx, AMH_EINVAL, "window too large for shared memory");
+    a.groups = ctx->lgroups_d[q];
+    a.ngroups = ctx->nlgroups[q];
+    const int per_sm = std::max(1, std::min((int)(ctx->smem_optin / std::max<size_t>(sm, 1)),
+                                            2048 / threads));
+    const int grid = std::max(1, std::min(a.ngroups, ctx->sm_count * per_sm));
+    CK(ctx, launch_local<R>(a, Gc, threads, grid, ctx->stream));
+  }
+  return AMH_OK;
+}
+
+amh_status check_ctx(amh_ctx* ctx) {
+  if (!ctx) return AMH_ESTATE;
+  if (ctx->broken) return AMH_ESTATE;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return AMH_OK;
+}
+
+void free_ctx(amh_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
+                  ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
+                  ctx->queue, ctx->err, ctx->trace, ctx->trace_count};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int q = 0; q < 6; ++q)
+    if (ctx->lgroups_d[q]) cudaFree(ctx->lgroups_d[q]);
+  delete ctx;
+}
+
+}  // namespace
+
+extern "C" {
+
+void amh_options_default(amh_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = 32;
+  opt->resync_every = 1000;
+  opt->chains_per_cta = 0;
+  opt->threads_per_cta = 0;
+  opt->trace_chains = 0;
+  opt->trace_capacity = 0;
+  opt->lattice_K = 0;
+  opt->table_is_neglog = 0;
+  opt->stream = nullptr;
+}
+
+amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chains_per_protein,
+                    const float* torsions, const double* table, const double* edges, int B,
+                    const amh_options* opt) {
+  if (!out) return set_err(nullptr, AMH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_proteins < 1 || !L || !chains_per_protein || !torsions || !table || !edges)
+    return set_err(nullptr, AMH_EINVAL, "missing argument");
+  if (B < 2 || B > 256) return set_err(nullptr, AMH_EINVAL, "B must be in [2, 256]");
+  amh_options o;
+  if (opt)
+    o = *opt;
+  else
+    amh_options_default(&o);
+  if (o.precision != 32 && o.precision != 64)
+    return set_err(nullptr, AMH_EINVAL, "precision must be 32 or 64");
+  if (o.resync_every <= 0) o.resync_every = 1000;
+  if (o.chains_per_cta != 0 && o.chains_per_cta != 1 && o.chains_per_cta != 2 &&
+      o.chains_per_cta != 4 && o.chains_per_cta != 8)
+    return set_err(nullptr, AMH_EINVAL, "chains_per_cta must be 0, 1, 2, 4 or 8");
+  if (o.precision == 64 && o.chains_per_cta == 8)
+    return set_err(nullptr, AMH_EINVAL, "precision 64 allows at most 4 chains per CTA");
+  if (o.threads_per_cta != 0 && o.threads_per_cta != 128 && o.threads_per_cta != 256)
+    return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 128 or 256");
+  if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)
+    return set_err(nullptr, AMH_EINVAL, "negative option");
+  // bins: evenly spaced centres
+  for (int j = 0; j < B; ++j)
+    if (!(edges[j] < edges[j + 1]) || !std::isfinite(edges[j]))
+      return set_err(nullptr, AMH_EINVAL, "edges must be finite and ascending (last may be +inf)");
+  std::vector<double> cen(B);
+  for (int j = 0; j < B; ++j) {
+    if (std::isinf(edges[j + 1])) {
+      if (j == 0) return set_err(nullptr, AMH_EINVAL, "open first bin");
+      cen[j] = edges[j] + 0.5 * (edges[j] - edges[j - 1]);
+    } else {
+      cen[j] = 0.5 * (edges[j] + edges[j + 1]);
+    }
+  }
+  const double w = (cen[B - 1] - cen[0]) / (B - 1);
+  for (int j = 0; j + 1 < B; ++j)
+    if (std::fabs((cen[j + 1] - cen[j]) - w) > 1e-9 * w)
+      return set_err(nullptr, AMH_EINVAL, "bin centres are not evenly spaced");
+
+  amh_ctx* ctx = new amh_ctx();
+  ctx->opt = o;
+  ctx->precision = o.precision;
+  ctx->stream = (cudaStream_t)o.stream;
+  ctx->B = B;
+  ctx->Bp = ((B + 1) + 3) & ~3;
+  ctx->c0 = cen[0];
+  ctx->w = w;
+  ctx->nprot = n_proteins;
+  long long chain0 = 0, tors0 = 0, rows = 0;
+  for (int p = 0; p < n_proteins; ++p) {
+    if (L[p] < 2 || L[p] > 4096 || chains_per_protein[p] < 1) {
+      delete ctx;
+      return set_err(nullptr, AMH_EINVAL, "need 2 <= L <= 4096 and >= 1 chain per protein");
+    }
+    ProteinDev d;
+    d.L = L[p];
+    d.n = 2 * L[p];
+    d.tab_off = rows * ctx->Bp;
+    d.chain0 = (int)chain0;
+    d.nchains = chains_per_protein[p];
+    d.tors0 = tors0;
+    ctx->prot_h.push_back(d);
+    ctx->L.push_back(L[p]);
+    ctx->nch.push_back(chains_per_protein[p]);
+    ctx->t_host.push_back(0);
+    chain0 += chains_per_protein[p];
+    tors0 += (long long)chains_per_protein[p] * d.n;
+    rows += (long long)L[p] * (L[p] - 1) / 2;
+    ctx->Lmax = std::max(ctx->Lmax, L[p]);
+  }
+  if (chain0 > (1LL << 30)) {
+    delete ctx;
+    return set_err(nullptr, AMH_EINVAL, "too many chains");
+  }
+  ctx->nmax = 2 * ctx->Lmax;
+  ctx->total_chains = (int)chain0;
+  ctx->tors_total = tors0;
+  ctx->rows_total = rows;
+
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return set_err(nullptr, AMH_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return set_err(nullptr, AMH_ECUDA, cudaGetErrorString(e));
+  }
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+
+  auto bail = [&](amh_status st) {
+    g_free_error = ctx->msg;
+    free_ctx(ctx);
+    return st;
+  };
+#define CKI(call)                                                        \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return bail(cuda_fail(ctx, e_, #call));       \
+  } while (0)
+  const int nc = ctx->total_chains;
+  CKI(cudaMalloc(&ctx->tcount, sizeof(long long) * nc));
+  CKI(cudaMemset(ctx->tcount, 0, sizeof(long long) * nc));
+  CKI(cudaMalloc(&ctx->E_cur, sizeof(double) * nc));
+  CKI(cudaMalloc(&ctx->best_E, sizeof(double) * nc));
+  CKI(cudaMalloc(&ctx->acc, sizeof(long long) * nc));
+  CKI(cudaMemset(ctx->acc, 0, sizeof(long long) * nc));
+  CKI(cudaMalloc(&ctx->prot_d, sizeof(ProteinDev) * n_proteins));
+  CKI(cudaMemcpy(ctx->prot_d, ctx->prot_h.data(), sizeof(ProteinDev) * n_proteins,
+                 cudaMemcpyHostToDevice));
+  std::vector<int> cp(nc);
+  for (int p = 0; p < n_proteins; ++p)
+    for (int c = 0; c < ctx->nch[p]; ++c) cp[ctx->prot_h[p].chain0 + c] = p;
+  CKI(cudaMalloc(&ctx->chain_prot_d, sizeof(int) * nc));
+  CKI(cudaMemcpy(ctx->chain_prot_d, cp.data(), sizeof(int) * nc, cudaMemcpyHostToDevice));
+  CKI(cudaMalloc(&ctx->queue, sizeof(int)));
+  CKI(cudaMalloc(&ctx->err, sizeof(int)));
+  CKI(cudaMemset(ctx->err, 0, sizeof(int)));
+  if (o.trace_chains > 0 && o.trace_capacity > 0) {
+    const int tc = std::min(o.trace_chains, nc);
+    ctx->opt.trace_chains = tc;
+    CKI(cudaMalloc(&ctx->trace, sizeof(TraceRec) * (size_t)tc * o.trace_capacity));
+    CKI(cudaMalloc(&ctx->trace_count, sizeof(long long) * tc));
+    CKI(cudaMemset(ctx->trace_count, 0, sizeof(long long) * tc));
+  } else {
+    ctx->opt.trace_chains = 0;
+  }
+  // the memsets above ran on the legacy stream; a non-blocking context
+  // stream is not ordered after it
+  CKI(cudaDeviceSynchronize());
+#undef CKI
+  amh_status st = ctx->precision == 64 ? init_impl<double>(ctx, torsions, table)
+                                       : init_impl<float>(ctx, torsions, table);
+  if (st != AMH_OK) return bail(st);
+  *out = ctx;
+  return AMH_OK;
+}
+
+amh_status amh_energy(amh_ctx* ctx, double* E_out) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  st = ctx->precision == 64 ? run_energy<double>(ctx) : run_energy<float>(ctx);
+  if (st) return st;
+  if (E_out) {
+    CK(ctx, cudaMemcpyAsync(E_out, ctx->E_cur, sizeof(double) * ctx->total_chains,
+                            cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(E_out)) return check_err_flag(ctx);
+  }
+  return AMH_OK;
+}
+
+static amh_status sweep_common(amh_ctx* ctx, int mode, int window, double T, double sigma,
+                               long long steps, int are_sweeps, unsigned long long seed,
+                               long long* accepted_out) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (mode != AMH_LOCAL && mode != AMH_GLOBAL) return set_err(ctx, AMH_EINVAL, "bad mode");
+  if (!(T > 0) || !std::isfinite(T)) return set_err(ctx, AMH_EINVAL, "T must be positive");
+  if (!std::isfinite(sigma)) return set_err(ctx, AMH_EINVAL, "sigma must be finite");
+  if (steps < 0) return set_err(ctx, AMH_EINVAL, "steps must be >= 0");
+  if (mode == AMH_LOCAL) {
+    if (window < 0 || window > 64) return set_err(ctx, AMH_EINVAL, "window must be in [0, 64]");
+    for (int p = 0; p < ctx->nprot; ++p) {
+      const long long n = 2LL * ctx->L[p];
+      if (ctx->t_host[p] % n != 0 || (!are_sweeps && steps % n != 0))
+        return set_err(ctx, AMH_EINVAL, "local sweeps need whole sweeps (t and steps multiples of n)");
+    }
+  }
+  if (steps > 0) {
+    st = ctx->precision == 64
+             ? sweep_impl<double>(ctx, mode, window, T, sigma, steps, are_sweeps, seed)
+             : sweep_impl<float>(ctx, mode, window, T, sigma, steps, are_sweeps, seed);
+    if (st) return st;
+  } else {
+    CK(ctx, cudaMemsetAsync(ctx->acc, 0, sizeof(long long) * ctx->total_chains, ctx->stream));
+  }
+  for (int p = 0; p < ctx->nprot; ++p)
+    ctx->t_host[p] += are_sweeps ? steps * 2LL * ctx->L[p] : steps;
+  if (accepted_out) {
+    CK(ctx, cudaMemcpyAsync(accepted_out, ctx->acc, sizeof(long long) * ctx->total_chains,
+                            cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(accepted_out)) return check_err_flag(ctx);
+  }
+  return AMH_OK;
+}
+
+amh_status amh_sweep(amh_ctx* ctx, int mode, int window, double T, double sigma_rad,
+                     long long steps, unsigned long long seed, long long* accepted_out) {
+  return sweep_common(ctx, mode, window, T, sigma_rad, steps, 0, seed, accepted_out);
+}
+
+amh_status amh_sweeps(amh_ctx* ctx, int mode, int window, double T, double sigma_rad,
+                      long long nsweeps, unsigned long long seed, long long* accepted_out) {
+  return sweep_common(ctx, mode, window, T, sigma_rad, nsweeps, 1, seed, accepted_out);
+}
+
+amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, double* E_out,
+                    void* dE_dtheta) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (protein < 0 || protein >= ctx->nprot || batch < 0)
+    return set_err(ctx, AMH_EINVAL, "bad protein or batch");
+  if (batch == 0) return AMH_OK;
+  if (!is_device_ptr(theta) || !is_device_ptr(E_out) || !is_device_ptr(dE_dtheta))
+    return set_err(ctx, AMH_EINVAL, "amh_grad needs device pointers");
+  const int L = ctx->L[protein];
+  const size_t esz = ctx->precision == 64 ? 8 : 4;
+  const size_t sm = ((esz * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1);
+  if (sm > ctx->smem_optin) return set_err(ctx, AMH_EINVAL, "protein too long for amh_grad");
+  if (ctx->precision == 64) {
+    CK(ctx, launch_grad<double>(&ctx->prot_h[protein], protein, L, (const double*)theta, batch,
+                                E_out, (double*)dE_dtheta, make_tab<double>(ctx),
+                                make_geom<double>(), ctx->stream));
+  } else {
+    CK(ctx, launch_grad<float>(&ctx->prot_h[protein], protein, L, (const float*)theta, batch,
+                               E_out, (float*)dE_dtheta, make_tab<float>(ctx),
+                               make_geom<float>(), ctx->stream));
+  }
+  return AMH_OK;
+}
+
+amh_status amh_get_state(amh_ctx* ctx, float* torsions_out, double* E_out, double* best_E,
+                         float* best_torsions) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  bool host = false;
+  const long long nt = ctx->tors_total;
+  auto out_tors = [&](const void* src, float* dst) -> amh_status {
+    if (!dst) return AMH_OK;
+    if (ctx->precision == 64) {
+      CK(ctx, launch_convert_out<double>((const double*)src, ctx->f32buf, nt, ctx->stream));
+      CK(ctx, cudaMemcpyAsync(dst, ctx->f32buf, sizeof(float) * nt, cudaMemcpyDefault, ctx->stream));
+    } else {
+      CK(ctx, cudaMemcpyAsync(dst, src, sizeof(float) * nt, cudaMemcpyDefault, ctx->stream));
+    }
+    if (!is_device_ptr(dst)) host = true;
+    if (ctx->precision == 64) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return AMH_OK;
+  };
+  st = out_tors(ctx->theta, torsions_out);
+  if (st) return st;
+  st = out_tors(ctx->best_theta, best_torsions);
+  if (st) return st;
+  if (E_out) {
+    CK(ctx, cudaMemcpyAsync(E_out, ctx->E_cur, sizeof(double) * ctx->total_chains,
+                            cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(E_out)) host = true;
+  }
+  if (best_E) {
+    CK(ctx, cudaMemcpyAsync(best_E, ctx->best_E, sizeof(double) * ctx->total_chains,
+                            cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(best_E)) host = true;
+  }
+  if (host) CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return AMH_OK;
+}
+
+amh_status amh_set_state(amh_ctx* ctx, const float* torsions) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!torsions) return set_err(ctx, AMH_EINVAL, "torsions is NULL");
+  const long long nt = ctx->tors_total;
+  CK(ctx, cudaMemcpyAsync(ctx->f32buf, torsions, sizeof(float) * nt, cudaMemcpyDefault,
+                          ctx->stream));
+  if (ctx->precision == 64) {
+    CK(ctx, launch_convert_in<double>(ctx->f32buf, (double*)ctx->theta, nt, ctx->stream));
+    st = run_energy<double>(ctx);
+  } else {
+    CK(ctx, launch_convert_in<float>(ctx->f32buf, (float*)ctx->theta, nt, ctx->stream));
+    st = run_energy<float>(ctx);
+  }
+  if (st) return st;
+  if (!is_device_ptr(torsions)) CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return AMH_OK;
+}
+
+amh_status amh_noisy_restart(amh_ctx* ctx, double sd_rad, unsigned long long seed) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!std::isfinite(sd_rad) || sd_rad < 0) return set_err(ctx, AMH_EINVAL, "bad sd");
+  if (ctx->precision == 64) {
+    CK(ctx, launch_noisy<double>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains, ctx->nmax,
+                                 (double*)ctx->theta, sd_rad, seed, ctx->stream));
+    return run_energy<double>(ctx);
+  }
+  CK(ctx, launch_noisy<float>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains, ctx->nmax,
+                              (float*)ctx->theta, (float)sd_rad, seed, ctx->stream));
+  return run_energy<float>(ctx);
+}
+
+amh_status amh_get_trace(amh_ctx* ctx, int chain, amh_trace_rec* out, long long* count) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!ctx->trace || chain < 0 || chain >= ctx->opt.trace_chains)
+    return set_err(ctx, AMH_EINVAL, "chain is not traced");
+  long long cnt = 0;
+  CK(ctx, cudaMemcpyAsync(&cnt, ctx->trace_count + chain, sizeof(long long),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (count) *count = cnt;
+  if (out && cnt > 0) {
+    static_assert(sizeof(amh_trace_rec) == sizeof(TraceRec), "trace record layout");
+    CK(ctx, cudaMemcpyAsync(out, ctx->trace + (size_t)chain * ctx->opt.trace_capacity,
+                            sizeof(TraceRec) * (size_t)cnt, cudaMemcpyDefault, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return AMH_OK;
+}
+
+amh_status amh_counter(amh_ctx* ctx, int chain, long long* t) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (chain < 0 || chain >= ctx->total_chains || !t) return set_err(ctx, AMH_EINVAL, "bad chain");
+  CK(ctx, cudaMemcpyAsync(t, ctx->tcount + chain, sizeof(long long), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return AMH_OK;
+}
+
+amh_status amh_philox(unsigned long long seed, unsigned chain, unsigned long long t0,
+                      unsigned stream, long long count, unsigned* words_out, float* z_out,
+                      float* u_out) {
+  if (count < 0) return set_err(nullptr, AMH_EINVAL, "count < 0");
+  if (count == 0) return AMH_OK;
+  uint4* w = nullptr;
+  float *z = nullptr, *u = nullptr;
+  auto fail = [&](cudaError_t e, const char* what) {
+    if (w) cudaFree(w);
+    if (z) cudaFree(z);
+    if (u) cudaFree(u);
+    return set_err(nullptr, AMH_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&w, sizeof(uint4) * count)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&z, sizeof(float) * count)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&u, sizeof(float) * count)) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = launch_philox_fill(seed, chain, t0, stream, count, w, z, u, 0)) != cudaSuccess)
+    return fail(e, "philox kernel");
+  if (words_out && (e = cudaMemcpy(words_out, w, sizeof(uint4) * count, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(e, "cudaMemcpy");
+  if (z_out && (e = cudaMemcpy(z_out, z, sizeof(float) * count, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(e, "cudaMemcpy");
+  if (u_out && (e = cudaMemcpy(u_out, u, sizeof(float) * count, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(e, "cudaMemcpy");
+  cudaFree(w);
+  cudaFree(z);
+  cudaFree(u);
+  return AMH_OK;
+}
+
+const char* amh_last_error(const amh_ctx* ctx) {
+  return ctx ? ctx->msg.c_str() : g_free_error.c_str();
+}
+
+amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta) {
+  if (!ctx) return AMH_ESTATE;
+  if (chains_per_cta) *chains_per_cta = ctx->C;
+  if (threads_per_cta) *threads_per_cta = ctx->threads;
+  return AMH_OK;
+}
+
+void amh_destroy(amh_ctx* ctx) { free_ctx(ctx); }
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+// amh_device.cuh -- device-side building blocks of the AMH kernels (sm_103a).
+//
+// Philox4x32-10 (Salmon et al., SC'11), Box-Muller, NeRF placement with
+// ideal geometry (Parsons et al. 2005; the paper only says x = G(s),
+// Sec. 2.1), rigid rotation about a bond axis (Sec. 2.4, "Proposal
+// Generation"), and the interpolated -ln p pair term of Eq. 5.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace amh {
+
+// ------------------------------------------------------------------ types
+template <class R>
+struct V3 {
+  R x, y, z;
+};
+
+template <class R>
+__device__ __forceinline__ V3<R> v3(R x, R y, R z) {
+  V3<R> r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  return r;
+}
+template <class R>
+__device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) {
+  return v3<R>(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+template <class R>
+__device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) {
+  return v3<R>(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+template <class R>
+__device__ __forceinline__ V3<R> operator*(V3<R> a, R s) {
+  return v3<R>(a.x * s, a.y * s, a.z * s);
+}
+template <class R>
+__device__ __forceinline__ R dot(V3<R> a, V3<R> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <class R>
+__device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+  return v3<R>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ void sincos_(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_(double a, double* s, double* c) { sincos(a, s, c); }
+
+template <class R>
+__device__ __forceinline__ V3<R> unit(V3<R> a) {
+  return a * rsqrt_(dot(a, a));
+}
+
+// Euclidean distance.  FP32: d2 * rsqrt(d2) (one MUFU op); FP64: sqrt.
+__device__ __forceinline__ float dist_(V3<float> a, V3<float> b) {
+  V3<float> d = a - b;
+  float d2 = fmaxf(dot(d, d), 1e-30f);
+  return d2 * rsqrtf(d2);
+}
+__device__ __forceinline__ double dist_(V3<double> a, V3<double> b) {
+  V3<double> d = a - b;
+  return sqrt(dot(d, d));
+}
+
+// ------------------------------------------------------------------ geometry
+// Ideal geometry as (-bond cos(angle), bond sin(angle)) pairs, filled on
+// the host in double precision (see amh.h for the values).
+template <class R>
+struct Geom {
+  R bNCA, bCAC;                  // N-CA, CA-C bond lengths (first residue)
+  R cosNCAC, sinNCAC;            // N-CA-C angle
+  R pN_c, pN_s;                  // N(i+1):  bond C-N,  angle CA-C-N
+  R pCA_c, pCA_s;                // CA(i+1): bond N-CA, angle C-N-CA
+  R pC_c, pC_s;                  // C(i+1):  bond CA-C, angle N-CA-C
+  R pCB_c, pCB_s;                // CB:      bond CA-CB, angle C-CA-CB
+  R cbT_c, cbT_s;                // CB improper dihedral N-C-CA-CB (cos, sin)
+};
+
+// NeRF: atom D bonded to C with the given (-b cos a, b sin a) and dihedral
+// A-B-C-D of cosine ct and sine st.
+template <class R>
+__device__ __forceinline__ V3<R> place(V3<R> A, V3<R> B, V3<R> C, R pc, R ps, R ct, R st) {
+  V3<R> bc = unit(C - B);
+  V3<R> nrm = unit(cross(B - A, bc));
+  V3<R> m = cross(nrm, bc);
+  R py = ps * ct, pz = ps * st;
+  return v3<R>(C.x + bc.x * pc + m.x * py + nrm.x * pz, C.y + bc.y * pc + m.y * py + nrm.y * pz,
+               C.z + bc.z * pc + m.z * py + nrm.z * pz);
+}
+
+// Canonical frame of a chain's (or window's) first residue.
+template <class R>
+__device__ __forceinline__ void first_residue(const Geom<R>& g, V3<R>& N, V3<R>& CA, V3<R>& C) {
+  N = v3<R>(R(0), R(0), R(0));
+  CA = v3<R>(g.bNCA, R(0), R(0));
+  C = v3<R>(g.bNCA - g.bCAC * g.cosNCAC, g.bCAC * g.sinNCAC, R(0));
+}
+
+// Next residue from the previous one: psi_i, omega = 180 deg, phi_{i+1}.
+template <class R>
+__device__ __forceinline__ void next_residue(const Geom<R>& g, V3<R>& N, V3<R>& CA, V3<R>& C,
+                                             R psi, R phi) {
+  R sp, cp, sf, cf;
+  sincos_(psi, &sp, &cp);
+  sincos_(phi, &sf, &cf);
+  V3<R> N1 = place(N, CA, C, g.pN_c, g.pN_s, cp, sp);
+  V3<R> CA1 = place(CA, C, N1, g.pCA_c, g.pCA_s, R(-1), R(0));
+  V3<R> C1 = place(C, N1, CA1, g.pC_c, g.pC_s, cf, sf);
+  N = N1;
+  CA = CA1;
+  C = C1;
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> cbeta(const Geom<R>& g, V3<R> N, V3<R> CA, V3<R> C) {
+  return place(N, C, CA, g.pCB_c, g.pCB_s, g.cbT_c, g.cbT_s);
+}
+
+// Affine map x -> M x + t (M row-major), stored as 12 values.
+template <class R>
+struct Aff {
+  R m[9];
+  R t[3];
+};
+
+template <class R>
+__device__ __forceinline__ V3<R> apply(const Aff<R>& A, V3<R> x) {
+  return v3<R>(fma(A.m[0], x.x, fma(A.m[1], x.y, fma(A.m[2], x.z, A.t[0]))),
+               fma(A.m[3], x.x, fma(A.m[4], x.y, fma(A.m[5], x.z, A.t[1]))),
+               fma(A.m[6], x.x, fma(A.m[7], x.y, fma(A.m[8], x.z, A.t[2]))));
+}
+
+// Right-handed rotation by angle `ang` about the axis through P towards Q.
+// Raising a dihedral by delta turns the far-side atoms by +delta about the
+// bond from its second to its third atom.
+template <class R>
+__device__ __forceinline__ Aff<R> rotation(V3<R> P, V3<R> Q, R ang) {
+  V3<R> u = unit(Q - P);
+  R s, c;
+  sincos_(ang, &s, &c);
+  R oc = R(1) - c;
+  Aff<R> A;
+  A.m[0] = c + u.x * u.x * oc;
+  A.m[1] = u.x * u.y * oc - u.z * s;
+  A.m[2] = u.x * u.z * oc + u.y * s;
+  A.m[3] = u.y * u.x * oc + u.z * s;
+  A.m[4] = c + u.y * u.y * oc;
+  A.m[5] = u.y * u.z * oc - u.x * s;
+  A.m[6] = u.z * u.x * oc - u.y * s;
+  A.m[7] = u.z * u.y * oc + u.x * s;
+  A.m[8] = c + u.z * u.z * oc;
+  // t = P - M P
+  A.t[0] = P.x - (A.m[0] * P.x + A.m[1] * P.y + A.m[2] * P.z);
+  A.t[1] = P.y - (A.m[3] * P.x + A.m[4] * P.y + A.m[5] * P.z);
+  A.t[2] = P.z - (A.m[6] * P.x + A.m[7] * P.y + A.m[8] * P.z);
+  return A;
+}
+
+// B o A (apply A first).
+template <class R>
+__device__ __forceinline__ Aff<R> compose(const Aff<R>& B, const Aff<R>& A) {
+  Aff<R> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      r.m[3 * i + j] = B.m[3 * i] * A.m[j] + B.m[3 * i + 1] * A.m[3 + j] + B.m[3 * i + 2] * A.m[6 + j];
+    r.t[i] = B.m[3 * i] * A.t[0] + B.m[3 * i + 1] * A.t[1] + B.m[3 * i + 2] * A.t[2] + B.t[i];
+  }
+  return r;
+}
+
+template <class R>
+__device__ __forceinline__ Aff<R> identity_map() {
+  Aff<R> A;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A.m[i] = (i % 4 == 0) ? R(1) : R(0);
+  A.t[0] = A.t[1] = A.t[2] = R(0);
+  return A;
+}
+
+// ------------------------------------------------------------------ table
+// Pair term of Eq. 5: -ln p interpolated linearly between evenly spaced bin
+// centres c_j = c0 + j w, flat outside [c_0, c_{B-1}].  Rows are padded to
+// Bp >= B+1 entries with copies of the last value, so j = B-1 reads a
+// valid neighbour.
+template <class R>
+struct Tab {
+  const R* __restrict__ E;  // [rows][Bp]
+  R inv_w;                  // 1 / w
+  R off;                    // -c0 / w
+  R umax;                   // B - 1
+  int Bp;
+};
+
+template <class R>
+__device__ __forceinline__ R pair_term(const R* __restrict__ row, R d, const Tab<R>& tb) {
+  R u = fma(d, tb.inv_w, tb.off);
+  u = fmin(fmax(u, R(0)), tb.umax);
+  int j = (int)u;
+  R t = u - (R)j;
+  R e0 = __ldg(row + j);
+  R e1 = __ldg(row + j + 1);
+  return fma(t, e1 - e0, e0);
+}
+
+// Value and slope d e / d d (zero on the flat ends).
+template <class R>
+__device__ __forceinline__ R pair_term_slope(const R* __restrict__ row, R d, const Tab<R>& tb,
+                                             R* slope) {
+  R u0 = fma(d, tb.inv_w, tb.off);
+  R u = fmin(fmax(u0, R(0)), tb.umax);
+  int j = (int)u;
+  R t = u - (R)j;
+  R e0 = __ldg(row + j);
+  R e1 = __ldg(row + j + 1);
+  *slope = (u0 >= R(0) && u0 < tb.umax) ? (e1 - e0) * tb.inv_w : R(0);
+  return fma(t, e1 - e0, e0);
+}
+
+// Row r(a,b) = a L - a(a+1)/2 + (b-a-1), a < b.
+__device__ __forceinline__ int row_of(int L, int a, int b) {
+  return a * L - ((a * (a + 1)) >> 1) + (b - a - 1);
+}
+
+// ------------------------------------------------------------------ RNG
+// Philox4x32-10: ten rounds of two 32x32->64 products by fixed odd
+// multipliers, XOR with the other words and the round key, word swap; the
+// key advances by fixed Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t a_lo = 0xD2511F53u * x.x, a_hi = __umulhi(0xD2511F53u, x.x);
+    const uint32_t b_lo = 0xCD9E8D57u * x.z, b_hi = __umulhi(0xCD9E8D57u, x.z);
+    x = make_uint4(b_hi ^ x.y ^ k.x, b_lo, a_hi ^ x.w ^ k.y, a_lo);
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint4 draw_words(unsigned long long seed, uint32_t chain,
+                                            unsigned long long t, uint32_t stream) {
+  return philox4x32_10(make_uint4(chain, (uint32_t)t, (uint32_t)(t >> 32), stream),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// ((w >> 9) + 1/2) / 2^23: exact in binary32.
+__device__ __forceinline__ float uniform23f(uint32_t w) {
+  return (float)((w >> 9)) * 0x1p-23f + 0x1p-24f;
+}
+__device__ __forceinline__ double uniform23d(uint32_t w) {
+  return (double)((w >> 9)) * 0x1p-23 + 0x1p-24;
+}
+
+// Box-Muller normal z and ln u for one proposal, in precision R.
+__device__ __forceinline__ void normal_and_lnu(uint4 w, float* z, float* lnu) {
+  float u0 = uniform23f(w.x), u1 = uniform23f(w.y), u2 = uniform23f(w.z);
+  *z = sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+  *lnu = logf(u2);
+}
+__device__ __forceinline__ void normal_and_lnu(uint4 w, double* z, double* lnu) {
+  double u0 = uniform23d(w.x), u1 = uniform23d(w.y), u2 = uniform23d(w.z);
+  *z = sqrt(-2.0 * log(u0)) * cospi(2.0 * u1);
+  *lnu = log(u2);
+}
+
+template <class R>
+__device__ __forceinline__ R pi_() {
+  return R(3.14159265358979323846);
+}
+
+// Wrap to (-pi, pi].
+template <class R>
+__device__ __forceinline__ R wrap_angle(R a) {
+  const R tp = R(2) * pi_<R>();
+  R w = a - tp * floor(a / tp + R(0.5));
+  if (w <= -pi_<R>()) w += tp;
+  if (w > pi_<R>()) w -= tp;
+  return w;
+}
+
+// Proposed torsion for current value th, normal z and step sigma; lattice
+// mode snaps to multiples of q = 2 pi / K.
+template <class R>
+__device__ __forceinline__ R propose(R th, R z, R sigma, int lattice_K) {
+  R prop = th + sigma * z;
+  if (lattice_K > 0) {
+    const R q = R(2) * pi_<R>() / R(lattice_K);
+    prop = q * rint(prop / q);
+  }
+  return wrap_angle(prop);
+}
+
+// ------------------------------------------------------------------ trace
+struct TraceRec {
+  int k;
+  int accept;
+  double theta_new;
+  double lnu;
+  double dE;
+};
+
+// ------------------------------------------------------------------ problem tables
+struct ProteinDev {
+  int L, n;
+  long long tab_off;  // element offset of row 0 of this protein's table
+  int chain0;         // first chain id of this protein
+  int nchains;
+  long long tors0;    // element offset of chain0's torsions
+};
+
+struct GroupDev {
+  int protein;
+  int chain0;   // absolute id of the group's first chain
+  int nchains;  // chains in this group (<= chains per CTA)
+  int pad;
+};
+
+}  // namespace amh

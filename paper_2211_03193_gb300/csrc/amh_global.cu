@@ -1,0 +1,546 @@
+// amh_global.cu -- global Metropolis sweeps and full-energy resync.
+//
+// One CTA runs a group of C chains of one protein in lock-step: they share
+// the torsion index k of every proposal (Alg. 1: k = 1..length(s) in
+// order), so the straddle block of pairs a < p(k) <= b (the only pairs
+// whose distance changes, Sec. 2.4 steps 2-3) reads the same distogram rows
+// for all C chains; lanes of a warp are (chain, slice) so one row fetch is
+// coalesced across the chains.  The proposal pair (2i-1, 2i) = (psi_{i-1},
+// phi_i) shares the pivot p = i, so both proposals are scored in one pass:
+// e(x), e(A1 x), e(A2 x) and e(A21 x) per pair give Delta-E of move 1 and
+// of move 2 after either outcome of move 1, exactly as in sequential
+// order.  The moving side of a proposal is the smaller one (energy is
+// invariant under rigid motion).  The running energy is kept in FP64 and
+// rebuilt from G(s) every resync_every proposals and at the end of a call.
+#include "amh_internal.h"
+
+namespace amh {
+
+namespace {
+
+constexpr int kFC = 16;  // fixed-side atoms per work item
+
+template <class R>
+struct AccT {
+  using T = float;
+};
+template <>
+struct AccT<double> {
+  using T = double;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Dynamic shared memory layout of a global-sweep CTA.
+template <class R, int C>
+struct Layout {
+  size_t theta, bb, cbx, cby, cbz, maps, part, ecur, thn, lnu, acc, commit, flag, total;
+  __host__ __device__ Layout(int Lmax, int nmax, int W) {
+    size_t o = 0;
+    theta = o; o = align16(o + sizeof(R) * (size_t)nmax * C);
+    bb = o;    o = align16(o + sizeof(R) * (size_t)Lmax * 9 * C);
+    cbx = o;   o = align16(o + sizeof(R) * (size_t)Lmax * C);
+    cby = o;   o = align16(o + sizeof(R) * (size_t)Lmax * C);
+    cbz = o;   o = align16(o + sizeof(R) * (size_t)Lmax * C);
+    maps = o;  o = align16(o + sizeof(R) * 36 * C);
+    part = o;  o = align16(o + sizeof(double) * 3 * (size_t)W * C);
+    ecur = o;  o = align16(o + sizeof(double) * C);
+    thn = o;   o = align16(o + sizeof(R) * 2 * C);
+    lnu = o;   o = align16(o + sizeof(R) * 2 * C);
+    acc = o;   o = align16(o + sizeof(long long) * C);
+    commit = o; o = align16(o + sizeof(int) * C);
+    flag = o;  o = align16(o + sizeof(int) * C);
+    total = o;
+  }
+};
+
+template <class R, int C>
+struct Shm {
+  R* theta;  // [k][C]
+  R* bb;     // [((i*3+atom)*3+xyz)][C], atom 0 N, 1 CA, 2 C
+  R* cbx;    // [i][C]
+  R* cby;
+  R* cbz;
+  R* maps;   // [C][36]: A1, A2, A21
+  double* part;  // [W][C][3]
+  double* ecur;  // [C]
+  R* thn;        // [2][C]
+  R* lnu;        // [2][C]
+  long long* acc;
+  int* commit;
+  int* flag;
+  __device__ Shm(unsigned char* base, const Layout<R, C>& l) {
+    theta = (R*)(base + l.theta);
+    bb = (R*)(base + l.bb);
+    cbx = (R*)(base + l.cbx);
+    cby = (R*)(base + l.cby);
+    cbz = (R*)(base + l.cbz);
+    maps = (R*)(base + l.maps);
+    part = (double*)(base + l.part);
+    ecur = (double*)(base + l.ecur);
+    thn = (R*)(base + l.thn);
+    lnu = (R*)(base + l.lnu);
+    acc = (long long*)(base + l.acc);
+    commit = (int*)(base + l.commit);
+    flag = (int*)(base + l.flag);
+  }
+  __device__ V3<R> cb(int i, int c) const {
+    return v3<R>(cbx[i * C + c], cby[i * C + c], cbz[i * C + c]);
+  }
+  __device__ V3<R> atom(int i, int a, int c) const {
+    const R* p = bb + (size_t)((i * 3 + a) * 3) * C + c;
+    return v3<R>(p[0], p[C], p[2 * C]);
+  }
+  __device__ void set_atom(int i, int a, int c, V3<R> v) {
+    R* p = bb + (size_t)((i * 3 + a) * 3) * C + c;
+    p[0] = v.x;
+    p[C] = v.y;
+    p[2 * C] = v.z;
+  }
+};
+
+// G(s) of chain slot c (one thread, serial along the chain).
+template <class R, int C>
+__device__ void build_chain(Shm<R, C>& s, const Geom<R>& g, int L, int c) {
+  V3<R> N, CA, Cc;
+  first_residue(g, N, CA, Cc);
+  for (int i = 0;; ++i) {
+    s.set_atom(i, 0, c, N);
+    s.set_atom(i, 1, c, CA);
+    s.set_atom(i, 2, c, Cc);
+    V3<R> cb = cbeta(g, N, CA, Cc);
+    s.cbx[i * C + c] = cb.x;
+    s.cby[i * C + c] = cb.y;
+    s.cbz[i * C + c] = cb.z;
+    if (i + 1 >= L) break;
+    next_residue(g, N, CA, Cc, s.theta[(2 * i + 1) * C + c], s.theta[(2 * i + 2) * C + c]);
+  }
+}
+
+// Reduce three per-lane partial sums over the slices of each chain and
+// over warps; results land in s.part[0..W) and the caller sums them.
+template <class R, int C>
+__device__ __forceinline__ void reduce3(Shm<R, C>& s, double a0, double a1, double a2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = C; off < 32; off <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+  }
+  if (lane < C) {
+    double* p = s.part + (size_t)(warp * C + lane) * 3;
+    p[0] = a0;
+    p[1] = a1;
+    p[2] = a2;
+  }
+}
+
+// Full energy of every chain slot from the current coordinates: FP32 (or
+// FP64) pair terms, FP64 sums (Eq. 5 over a<b).  Ends with s.ecur set.
+template <class R, int C>
+__device__ void full_energy(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, int L) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  constexpr int S = 32 / C;
+  const int c = lane % C, sl = lane / C;
+  const int gs = warp * S + sl, G = W * S;
+  const int nch = (L - 1 + kFC - 1) / kFC;
+  const int items = L * nch;
+  double acc = 0.0;
+  for (int it = gs; it < items; it += G) {
+    const int a = it / nch, ch = it - a * nch;
+    const int b0 = a + 1 + ch * kFC;
+    const int b1 = min(L, b0 + kFC);
+    if (b0 >= b1) continue;
+    const V3<R> xa = s.cb(a, c);
+    const R* row = tb.E + tab_off + (long long)row_of(L, a, b0) * tb.Bp;
+    typename AccT<R>::T part = 0;
+    for (int b = b0; b < b1; ++b, row += tb.Bp) part += pair_term(row, dist_(xa, s.cb(b, c)), tb);
+    acc += (double)part;
+  }
+  reduce3(s, acc, 0.0, 0.0);
+  __syncthreads();
+  if (threadIdx.x < C) {
+    double e = 0.0;
+    for (int w = 0; w < W; ++w) e += s.part[(size_t)(w * C + threadIdx.x) * 3];
+    s.ecur[threadIdx.x] = e;
+  }
+  __syncthreads();
+}
+
+template <class R, int C>
+__device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P) {
+  __syncthreads();
+  if (threadIdx.x < C) build_chain(s, a.geom, P.L, threadIdx.x);
+  __syncthreads();
+  full_energy(s, a.tab, P.tab_off, P.L);
+}
+
+template <class R, int C>
+__device__ __forceinline__ void load_aff(const R* src, Aff<R>& A) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A.m[i] = src[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) A.t[i] = src[9 + i];
+}
+
+template <class R>
+__device__ __forceinline__ void store_aff(R* dst, const Aff<R>& A) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dst[i] = A.m[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dst[9 + i] = A.t[i];
+}
+
+// Straddle-block Delta-E (moving side [m0, m1), fixed side [f0, f1)).
+template <class R, int C, bool FUSED>
+__device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, int L, int m0,
+                           int m1, int f0, int f1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  constexpr int S = 32 / C;
+  const int c = lane % C, sl = lane / C;
+  const int gs = warp * S + sl, G = W * S;
+  Aff<R> A1, A2, A21;
+  load_aff<R, C>(s.maps + 36 * c, A1);
+  if (FUSED) {
+    load_aff<R, C>(s.maps + 36 * c + 12, A2);
+    load_aff<R, C>(s.maps + 36 * c + 24, A21);
+  }
+  const int nF = f1 - f0;
+  const int nch = (nF + kFC - 1) / kFC;
+  const int items = (m1 - m0) * nch;
+  typename AccT<R>::T acc1 = 0, acc2 = 0, acc21 = 0;
+  for (int it = gs; it < items; it += G) {
+    const int mi = it / nch, ch = it - mi * nch;
+    const int m = m0 + mi;
+    const V3<R> xm = s.cb(m, c);
+    const V3<R> y1 = apply(A1, xm);
+    V3<R> y2, y21;
+    if (FUSED) {
+      y2 = apply(A2, xm);
+      y21 = apply(A21, xm);
+    }
+    const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
+    for (int f = fb; f < fe; ++f) {
+      const V3<R> xf = s.cb(f, c);
+      const int ra = min(f, m), rb = max(f, m);
+      const R* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
+      const R e0 = pair_term(row, dist_(xf, xm), tb);
+      const R e1 = pair_term(row, dist_(xf, y1), tb);
+      acc1 += e1 - e0;
+      if (FUSED) {
+        const R e2 = pair_term(row, dist_(xf, y2), tb);
+        const R e21 = pair_term(row, dist_(xf, y21), tb);
+        acc2 += e2 - e0;
+        acc21 += e21 - e1;
+      }
+    }
+  }
+  reduce3(s, (double)acc1, (double)acc2, (double)acc21);
+}
+
+// Apply each chain's committed map to its moving residues [m0, m1).
+template <class R, int C>
+__device__ void commit_moves(Shm<R, C>& s, int m0, int m1) {
+  const int total = (m1 - m0) * 4 * C;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int c = idx % C;
+    const int code = s.commit[c];
+    if (!code) continue;
+    const int rest = idx / C;
+    const int atom = rest & 3, i = m0 + (rest >> 2);
+    Aff<R> A;
+    load_aff<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
+    if (atom < 3) {
+      s.set_atom(i, atom, c, apply(A, s.atom(i, atom, c)));
+    } else {
+      V3<R> y = apply(A, s.cb(i, c));
+      s.cbx[i * C + c] = y.x;
+      s.cby[i * C + c] = y.y;
+      s.cbz[i * C + c] = y.z;
+    }
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void put_trace(const SweepArgs<R>& a, bool real, int chain, long long v,
+                                          int k, int acc, R thn, R lnu, double dE) {
+  if (real && chain < a.trace_chains && v < a.trace_cap) {
+    TraceRec r;
+    r.k = k;
+    r.accept = acc;
+    r.theta_new = (double)thn;
+    r.lnu = (double)lnu;
+    r.dE = dE;
+    a.trace[(size_t)chain * a.trace_cap + v] = r;
+  }
+}
+
+template <class R, int C>
+__device__ void load_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G,
+                           const ProteinDev& P) {
+  const int n = P.n;
+  for (int idx = threadIdx.x; idx < n * C; idx += blockDim.x) {
+    const int c = idx / n, k = idx - c * n;
+    R v = R(0);
+    if (c < G.nchains) v = a.theta[P.tors0 + (long long)(G.chain0 - P.chain0 + c) * n + k];
+    s.theta[k * C + c] = v;
+  }
+  if (threadIdx.x < C) s.acc[threadIdx.x] = 0;
+}
+
+// Write back torsions, counters, energies, accepted counts and best states.
+template <class R, int C>
+__device__ void store_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G,
+                            const ProteinDev& P, long long t_end, bool update_best) {
+  const int n = P.n;
+  if (threadIdx.x < C) {
+    const int c = threadIdx.x;
+    int better = 0;
+    if (c < G.nchains) {
+      const int chain = G.chain0 + c;
+      const double e = s.ecur[c];
+      if (!(e == e)) atomicOr(a.err, 1);  // NaN energy
+      a.E_cur[chain] = e;
+      a.tcount[chain] = t_end;
+      if (a.acc_out) a.acc_out[chain] = s.acc[c];
+      if (a.trace_count && chain < a.trace_chains)
+        a.trace_count[chain] = t_end < a.trace_cap ? t_end : a.trace_cap;
+      if (update_best && e < a.best_E[chain]) {
+        a.best_E[chain] = e;
+        better = 1;
+      }
+    }
+    s.flag[c] = better;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * C; idx += blockDim.x) {
+    const int c = idx / n, k = idx - c * n;
+    if (c >= G.nchains) continue;
+    const long long off = P.tors0 + (long long)(G.chain0 - P.chain0 + c) * n + k;
+    const R v = s.theta[k * C + c];
+    a.theta[off] = v;
+    if (s.flag[c]) a.best_theta[off] = v;
+  }
+}
+
+template <class R, int C>
+__device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G,
+                          const ProteinDev& P) {
+  const int L = P.L, n = P.n;
+  load_group(s, a, G, P);
+  const long long t0 = a.tcount[G.chain0];
+  const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
+  resync(s, a, P);
+  long long since = 0;
+  for (long long j = 0; j < steps;) {
+    if (since >= a.resync_every) {
+      resync(s, a, P);
+      since = 0;
+    }
+    const long long t = t0 + j;
+    const int k = (int)(t % n);
+    const bool fused = (k & 1) && (k + 1 < n) && (j + 1 < steps);
+    const int p = (k + 1) >> 1;
+    const bool up = p <= L - p;  // move the upstream side (it is the smaller)
+    const int m0 = up ? 0 : p, m1 = up ? p : L;
+    const int f0 = up ? p : 0, f1 = up ? L : p;
+    const bool dead = (k == 0) || (k == n - 1);
+    if (threadIdx.x < C) {
+      const int c = threadIdx.x;
+      const int chain = G.chain0 + c;
+      R z, lnu;
+      normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)t, 0u), &z, &lnu);
+      const R th = s.theta[k * C + c];
+      const R thn = propose(th, z, a.sigma, a.lattice_K);
+      s.thn[c] = thn;
+      s.lnu[c] = lnu;
+      if (!dead) {
+        const R d1 = wrap_angle(thn - th);
+        V3<R> P1, Q1;
+        if (k & 1) {  // psi_i about CA_i -> C_i
+          const int i = k >> 1;
+          P1 = s.atom(i, 1, c);
+          Q1 = s.atom(i, 2, c);
+        } else {      // phi_i about N_i -> CA_i
+          const int i = k >> 1;
+          P1 = s.atom(i, 0, c);
+          Q1 = s.atom(i, 1, c);
+        }
+        const Aff<R> A1 = rotation(P1, Q1, up ? -d1 : d1);
+        store_aff(s.maps + 36 * c, A1);
+        if (fused) {
+          R z2, lnu2;
+          normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)(t + 1), 0u), &z2,
+                         &lnu2);
+          const R th2 = s.theta[(k + 1) * C + c];
+          const R thn2 = propose(th2, z2, a.sigma, a.lattice_K);
+          s.thn[C + c] = thn2;
+          s.lnu[C + c] = lnu2;
+          const R d2 = wrap_angle(thn2 - th2);
+          const V3<R> P2 = s.atom(p, 0, c), Q2 = s.atom(p, 1, c);  // phi_p: N_p -> CA_p
+          const Aff<R> A2 = rotation(P2, Q2, up ? -d2 : d2);
+          store_aff(s.maps + 36 * c + 12, A2);
+          // after move 1 the axis of move 2 has moved with the far side
+          const V3<R> P2m = up ? P2 : apply(A1, P2);
+          const V3<R> Q2m = up ? Q2 : apply(A1, Q2);
+          const Aff<R> A2m = rotation(P2m, Q2m, up ? -d2 : d2);
+          store_aff(s.maps + 36 * c + 24, compose(A2m, A1));
+        }
+      }
+    }
+    __syncthreads();
+    if (dead) {
+      // phi_0 and psi_{L-1} move no C-beta: Delta-E = 0, always accepted
+      if (threadIdx.x < C) {
+        const int c = threadIdx.x;
+        const int chain = G.chain0 + c;
+        const int acc = (double)s.lnu[c] < -0.0 / a.T;
+        if (acc) s.theta[k * C + c] = s.thn[c];
+        s.acc[c] += acc;
+        put_trace(a, c < G.nchains, chain, t, k, acc, s.thn[c], s.lnu[c], 0.0);
+      }
+      __syncthreads();
+      j += 1;
+      since += 1;
+      continue;
+    }
+    if (fused)
+      pair_block<R, C, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+    else
+      pair_block<R, C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+    __syncthreads();
+    if (threadIdx.x < C) {
+      const int c = threadIdx.x;
+      const int chain = G.chain0 + c;
+      const int W = blockDim.x >> 5;
+      double d1 = 0.0, d2 = 0.0, d21 = 0.0;
+      for (int w = 0; w < W; ++w) {
+        const double* pp = s.part + (size_t)(w * C + c) * 3;
+        d1 += pp[0];
+        d2 += pp[1];
+        d21 += pp[2];
+      }
+      const int acc1 = (double)s.lnu[c] < -d1 / a.T;
+      int code = acc1;
+      double dE = acc1 ? d1 : 0.0;
+      if (acc1) s.theta[k * C + c] = s.thn[c];
+      put_trace(a, c < G.nchains, chain, t, k, acc1, s.thn[c], s.lnu[c], d1);
+      int acc2 = 0;
+      if (fused) {
+        const double e2 = acc1 ? d21 : d2;
+        acc2 = (double)s.lnu[C + c] < -e2 / a.T;
+        if (acc2) {
+          code = acc1 ? 3 : 2;
+          dE += e2;
+          s.theta[(k + 1) * C + c] = s.thn[C + c];
+        }
+        put_trace(a, c < G.nchains, chain, t + 1, k + 1, acc2, s.thn[C + c], s.lnu[C + c], e2);
+      }
+      s.ecur[c] += dE;
+      s.acc[c] += acc1 + acc2;
+      s.commit[c] = code;
+    }
+    __syncthreads();
+    commit_moves(s, m0, m1);
+    __syncthreads();
+    j += fused ? 2 : 1;
+    since += fused ? 2 : 1;
+  }
+  resync(s, a, P);
+  store_group(s, a, G, P, t0 + steps, true);
+}
+
+template <class R, int C>
+__global__ void __launch_bounds__(256) global_kernel(SweepArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_group;
+  const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);
+  Shm<R, C> s(smem, lay);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_group = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int g = s_group;
+    if (g >= a.ngroups) break;
+    const GroupDev G = a.groups[g];
+    const ProteinDev P = a.prot[G.protein];
+    run_group(s, a, G, P);
+  }
+}
+
+template <class R, int C>
+__global__ void __launch_bounds__(256) energy_kernel(SweepArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_group;
+  const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);
+  Shm<R, C> s(smem, lay);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_group = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int g = s_group;
+    if (g >= a.ngroups) break;
+    const GroupDev G = a.groups[g];
+    const ProteinDev P = a.prot[G.protein];
+    load_group(s, a, G, P);
+    resync(s, a, P);
+    if (threadIdx.x < C && threadIdx.x < G.nchains) {
+      const double e = s.ecur[threadIdx.x];
+      if (!(e == e)) atomicOr(a.err, 1);
+      a.E_cur[G.chain0 + threadIdx.x] = e;
+    }
+  }
+}
+
+}  // namespace
+
+template <class R, int C>
+size_t global_smem_bytes(int Lmax, int nmax, int threads) {
+  return Layout<R, C>(Lmax, nmax, threads / 32).total;
+}
+
+template <class R, int C>
+cudaError_t global_set_smem(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(global_kernel<R, C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(energy_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
+}
+
+template <class R, int C>
+cudaError_t global_occupancy(int threads, size_t smem, int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, global_kernel<R, C>, threads, smem);
+}
+
+template <class R, int C>
+cudaError_t launch_global(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st) {
+  const size_t sm = global_smem_bytes<R, C>(a.Lmax, a.nmax, threads);
+  global_kernel<R, C><<<grid, threads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class R, int C>
+cudaError_t launch_energy(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st) {
+  const size_t sm = global_smem_bytes<R, C>(a.Lmax, a.nmax, threads);
+  energy_kernel<R, C><<<grid, threads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define AMH_INST(R, C)                                                                      \
+  template size_t global_smem_bytes<R, C>(int, int, int);                                  \
+  template cudaError_t global_set_smem<R, C>(size_t);                                      \
+  template cudaError_t global_occupancy<R, C>(int, size_t, int*);                          \
+  template cudaError_t launch_global<R, C>(const SweepArgs<R>&, int, int, cudaStream_t);   \
+  template cudaError_t launch_energy<R, C>(const SweepArgs<R>&, int, int, cudaStream_t);
+
+AMH_INST(float, 1)
+AMH_INST(float, 2)
+AMH_INST(float, 4)
+AMH_INST(float, 8)
+AMH_INST(double, 1)
+AMH_INST(double, 2)
+AMH_INST(double, 4)
+
+}  // namespace amh

@@ -1,0 +1,97 @@
+// amh_internal.h -- launch arguments and launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "amh_device.cuh"
+
+namespace amh {
+
+// Arguments of a sweep / energy launch over chain groups.
+template <class R>
+struct SweepArgs {
+  const ProteinDev* prot;
+  const GroupDev* groups;
+  int ngroups;
+  int* queue;  // work counter, zeroed before the launch
+  R* theta;    // all chains' torsions (ragged, ProteinDev::tors0)
+  R* best_theta;
+  long long* tcount;  // per chain proposal counter
+  double* E_cur;
+  double* best_E;
+  long long* acc_out;  // per chain accepted count of this call (may be null)
+  Tab<R> tab;
+  Geom<R> geom;
+  double T;
+  R sigma;
+  unsigned long long seed;
+  long long steps;      // proposals per chain, or sweeps if steps_are_sweeps
+  int steps_are_sweeps;
+  int resync_every;
+  int lattice_K;
+  int window;           // local sweeps: d
+  int Lmax, nmax;       // smem sizing
+  TraceRec* trace;
+  int trace_chains;
+  long long trace_cap;
+  long long* trace_count;  // per traced chain, records written
+  int* err;
+};
+
+// Global sweeps (Eqs. 1-3, Alg. 1 first loop) and full-energy resync.
+template <class R, int C>
+cudaError_t launch_global(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st);
+template <class R, int C>
+cudaError_t launch_energy(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st);
+template <class R, int C>
+size_t global_smem_bytes(int Lmax, int nmax, int threads);
+template <class R, int C>
+cudaError_t global_set_smem(size_t bytes);
+template <class R, int C>
+cudaError_t global_occupancy(int threads, size_t smem, int* per_sm);
+
+// Local sweeps (Eqs. 4a-b, Eq. 6, Alg. 1 second loop).
+template <class R>
+cudaError_t launch_local(const SweepArgs<R>& a, int chains_per_cta, int threads, int grid,
+                         cudaStream_t st);
+template <class R>
+size_t local_smem_bytes(int nmax, int chains_per_cta, int threads, int window);
+template <class R>
+cudaError_t local_set_smem(size_t bytes);
+
+// Gradient of V for a batch of torsion vectors of one protein.
+// (prot_host: host copy of the protein's record; only tab_off is read.)
+template <class R>
+cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R* theta,
+                        int batch, double* E_out, R* grad, Tab<R> tab, Geom<R> geom,
+                        cudaStream_t st);
+
+// Table preparation: p (or -ln p) float64 -> padded R rows.
+template <class R>
+cudaError_t launch_prep_table(const double* p, long long rows, int B, int Bp, int neglog, R* out,
+                              cudaStream_t st);
+
+// Noisy restart over all chains.
+template <class R>
+cudaError_t launch_noisy(const ProteinDev* prot, const int* chain_prot, int nchains, int nmax,
+                         R* theta, R sd, unsigned long long seed, cudaStream_t st);
+
+// Best-state update after a global sweep or an energy call.
+template <class R>
+cudaError_t launch_best(const ProteinDev* prot, const int* chain_prot, int nchains, int nmax,
+                        const R* theta, R* best_theta, const double* E, double* best_E, int init,
+                        cudaStream_t st);
+
+// Conversions between the FP32 interface layout and the internal precision.
+template <class R>
+cudaError_t launch_convert_in(const float* src, R* dst, long long count, cudaStream_t st);
+template <class R>
+cudaError_t launch_convert_out(const R* src, float* dst, long long count, cudaStream_t st);
+
+cudaError_t launch_philox_fill(unsigned long long seed, unsigned chain, unsigned long long t0,
+                               unsigned stream, long long count, uint4* words, float* z, float* u,
+                               cudaStream_t st);
+
+}  // namespace amh

@@ -1,0 +1,274 @@
+// amh_misc.cu -- gradient of V, table preparation, noisy restart, best-state
+// bookkeeping, precision conversions and the Philox fill used for checking.
+#include "amh_internal.h"
+
+namespace amh {
+
+namespace {
+
+// ---------------------------------------------------------------- gradient
+// dV/ds_k for one torsion vector per CTA.  Changing s_k turns every C-beta
+// b >= p(k) about the bond axis (u, o), so dV/ds_k = sum_{b>=p} g_b .
+// (u x (x_b - o)) = u . (M_p - o x G_p) with g_b = dV/dx_b (pair forces),
+// G_p = sum_{b>=p} g_b, M_p = sum_{b>=p} x_b x g_b.  Pairs on the same side
+// of the pivot contribute forces that cancel in the sum.
+template <class R>
+__global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, const R* __restrict__ theta,
+                                                   double* __restrict__ E_out, R* __restrict__ grad,
+                                                   Tab<R> tb, Geom<R> geom) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = 2 * L;
+  R* X = (R*)smem;          // [4][L][3]: N, CA, C, CB
+  R* gb = X + 12 * L;       // [L][3] dV/dx_b
+  double* GM = (double*)(smem + (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15));  // [L+1][6]
+  __shared__ double wpart[32];
+  const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const R* th = theta + (size_t)v * n;
+  if (tid == 0) {
+    V3<R> N, CA, Cc;
+    first_residue(geom, N, CA, Cc);
+    for (int i = 0;; ++i) {
+      V3<R> cb = cbeta(geom, N, CA, Cc);
+      const V3<R> at[4] = {N, CA, Cc, cb};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        X[(q * L + i) * 3 + 0] = at[q].x;
+        X[(q * L + i) * 3 + 1] = at[q].y;
+        X[(q * L + i) * 3 + 2] = at[q].z;
+      }
+      if (i + 1 >= L) break;
+      next_residue(geom, N, CA, Cc, th[2 * i + 1], th[2 * i + 2]);
+    }
+  }
+  __syncthreads();
+  const R* CB = X + 9 * L;
+  double esum = 0.0;
+  for (int b = tid; b < L; b += nt) {
+    const V3<R> xb = v3<R>(CB[3 * b], CB[3 * b + 1], CB[3 * b + 2]);
+    R gx = 0, gy = 0, gz = 0;
+    R epart = 0;
+    for (int a = 0; a < L; ++a) {
+      if (a == b) continue;
+      const V3<R> xa = v3<R>(CB[3 * a], CB[3 * a + 1], CB[3 * a + 2]);
+      const int ra = min(a, b), rb = max(a, b);
+      const R* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
+      const V3<R> dlt = xb - xa;
+      const R d = sqrt(dot(dlt, dlt));
+      R sl;
+      const R e = pair_term_slope(row, d, tb, &sl);
+      const R f = d > R(0) ? sl / d : R(0);
+      gx += f * dlt.x;
+      gy += f * dlt.y;
+      gz += f * dlt.z;
+      if (a < b) epart += e;
+    }
+    gb[3 * b] = gx;
+    gb[3 * b + 1] = gy;
+    gb[3 * b + 2] = gz;
+    esum += (double)epart;
+  }
+  for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
+  if ((tid & 31) == 0) wpart[tid >> 5] = esum;
+  __syncthreads();
+  if (tid == 0) {
+    double e = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) e += wpart[w];
+    E_out[v] = e;
+    // suffix sums over b >= p in FP64
+    double G0 = 0, G1 = 0, G2 = 0, M0 = 0, M1 = 0, M2 = 0;
+    double* row = GM + (size_t)L * 6;
+    row[0] = row[1] = row[2] = row[3] = row[4] = row[5] = 0.0;
+    for (int b = L - 1; b >= 0; --b) {
+      const double x0 = CB[3 * b], x1 = CB[3 * b + 1], x2 = CB[3 * b + 2];
+      const double g0 = gb[3 * b], g1 = gb[3 * b + 1], g2 = gb[3 * b + 2];
+      G0 += g0;
+      G1 += g1;
+      G2 += g2;
+      M0 += x1 * g2 - x2 * g1;
+      M1 += x2 * g0 - x0 * g2;
+      M2 += x0 * g1 - x1 * g0;
+      double* r = GM + (size_t)b * 6;
+      r[0] = G0; r[1] = G1; r[2] = G2; r[3] = M0; r[4] = M1; r[5] = M2;
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < n; k += nt) {
+    const int i = k >> 1, p = (k + 1) >> 1;
+    double val = 0.0;
+    if (k != 0 && p < L) {
+      const int qa = (k & 1) ? 1 : 0, qb = (k & 1) ? 2 : 1;  // psi: CA->C, phi: N->CA
+      const double o0 = X[(qa * L + i) * 3], o1 = X[(qa * L + i) * 3 + 1], o2 = X[(qa * L + i) * 3 + 2];
+      double u0 = X[(qb * L + i) * 3] - o0, u1 = X[(qb * L + i) * 3 + 1] - o1,
+             u2 = X[(qb * L + i) * 3 + 2] - o2;
+      const double un = rsqrt(u0 * u0 + u1 * u1 + u2 * u2);
+      u0 *= un; u1 *= un; u2 *= un;
+      const double* r = GM + (size_t)p * 6;
+      const double t0 = r[3] - (o1 * r[2] - o2 * r[1]);
+      const double t1 = r[4] - (o2 * r[0] - o0 * r[2]);
+      const double t2 = r[5] - (o0 * r[1] - o1 * r[0]);
+      val = u0 * t0 + u1 * t1 + u2 * t2;
+    }
+    grad[(size_t)v * n + k] = (R)val;
+  }
+}
+
+// ---------------------------------------------------------------- table
+template <class R>
+__global__ void prep_table_kernel(const double* __restrict__ p, long long rows, int B, int Bp,
+                                  int neglog, R* __restrict__ out) {
+  const long long total = rows * Bp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / Bp;
+    int j = (int)(i - r * Bp);
+    if (j >= B) j = B - 1;  // padding repeats the last bin
+    double q = p[r * B + j];
+    double e = neglog ? q : -log(q > 1e-300 ? q : 1e-300);
+    out[i] = (R)e;
+  }
+}
+
+// ---------------------------------------------------------------- noisy restart
+template <class R>
+__global__ void noisy_kernel(const ProteinDev* __restrict__ prot, const int* __restrict__ chain_prot,
+                             R* __restrict__ theta, R sd, unsigned long long seed) {
+  const int chain = blockIdx.y;
+  const ProteinDev P = prot[chain_prot[chain]];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.n) return;
+  R z, lnu;
+  normal_and_lnu(draw_words(seed, (uint32_t)chain, (unsigned long long)k, 1u), &z, &lnu);
+  R* th = theta + P.tors0 + (long long)(chain - P.chain0) * P.n;
+  th[k] = wrap_angle(th[k] + sd * z);
+}
+
+// ---------------------------------------------------------------- best state
+template <class R>
+__global__ void best_kernel(const ProteinDev* __restrict__ prot, const int* __restrict__ chain_prot,
+                            const R* __restrict__ theta, R* __restrict__ best_theta,
+                            const double* __restrict__ E, double* __restrict__ best_E, int init) {
+  const int chain = blockIdx.x;
+  const ProteinDev P = prot[chain_prot[chain]];
+  __shared__ int better;
+  if (threadIdx.x == 0) {
+    better = init || E[chain] < best_E[chain];
+    if (better) best_E[chain] = E[chain];
+  }
+  __syncthreads();
+  if (!better) return;
+  const long long off = P.tors0 + (long long)(chain - P.chain0) * P.n;
+  for (int k = threadIdx.x; k < P.n; k += blockDim.x) best_theta[off + k] = theta[off + k];
+}
+
+// ---------------------------------------------------------------- conversions
+template <class R>
+__global__ void convert_in_kernel(const float* __restrict__ src, R* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (R)src[i];
+}
+template <class R>
+__global__ void convert_out_kernel(const R* __restrict__ src, float* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// ---------------------------------------------------------------- Philox fill
+__global__ void philox_kernel(unsigned long long seed, unsigned chain, unsigned long long t0,
+                              unsigned stream, long long count, uint4* words, float* z, float* u) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const uint4 w = draw_words(seed, chain, t0 + (unsigned long long)i, stream);
+    words[i] = w;
+    float zz, ll;
+    normal_and_lnu(w, &zz, &ll);
+    if (z) z[i] = zz;
+    if (u) u[i] = uniform23f(w.z);
+  }
+}
+
+inline int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 65535LL * 8) g = 65535LL * 8;
+  return (int)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+template <class R>
+cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R* theta, int batch,
+                        double* E_out, R* grad, Tab<R> tab, Geom<R> geom, cudaStream_t st) {
+  (void)protein;
+  const size_t sm = (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1);
+  cudaError_t e =
+      cudaFuncSetAttribute(grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  if (batch <= 0) return cudaSuccess;
+  grad_kernel<R><<<batch, 256, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab, geom);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_prep_table(const double* p, long long rows, int B, int Bp, int neglog, R* out,
+                              cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  prep_table_kernel<R><<<grid_for(rows * Bp, 256), 256, 0, st>>>(p, rows, B, Bp, neglog, out);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_noisy(const ProteinDev* prot, const int* chain_prot, int nchains, int nmax,
+                         R* theta, R sd, unsigned long long seed, cudaStream_t st) {
+  dim3 grid((nmax + 127) / 128, nchains);
+  noisy_kernel<R><<<grid, 128, 0, st>>>(prot, chain_prot, theta, sd, seed);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_best(const ProteinDev* prot, const int* chain_prot, int nchains, int nmax,
+                        const R* theta, R* best_theta, const double* E, double* best_E, int init,
+                        cudaStream_t st) {
+  (void)nmax;
+  best_kernel<R><<<nchains, 128, 0, st>>>(prot, chain_prot, theta, best_theta, E, best_E, init);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_convert_in(const float* src, R* dst, long long count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  convert_in_kernel<R><<<grid_for(count, 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_convert_out(const R* src, float* dst, long long count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  convert_out_kernel<R><<<grid_for(count, 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_fill(unsigned long long seed, unsigned chain, unsigned long long t0,
+                               unsigned stream, long long count, uint4* words, float* z, float* u,
+                               cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  philox_kernel<<<grid_for(count, 256), 256, 0, st>>>(seed, chain, t0, stream, count, words, z, u);
+  return cudaGetLastError();
+}
+
+#define AMH_MISC_INST(R)                                                                           \
+  template cudaError_t launch_grad<R>(const ProteinDev*, int, int, const R*, int, double*, R*,     \
+                                      Tab<R>, Geom<R>, cudaStream_t);                              \
+  template cudaError_t launch_prep_table<R>(const double*, long long, int, int, int, R*,           \
+                                            cudaStream_t);                                         \
+  template cudaError_t launch_noisy<R>(const ProteinDev*, const int*, int, int, R*, R,             \
+                                       unsigned long long, cudaStream_t);                          \
+  template cudaError_t launch_best<R>(const ProteinDev*, const int*, int, int, const R*, R*,        \
+                                      const double*, double*, int, cudaStream_t);                  \
+  template cudaError_t launch_convert_in<R>(const float*, R*, long long, cudaStream_t);            \
+  template cudaError_t launch_convert_out<R>(const R*, float*, long long, cudaStream_t);
+
+AMH_MISC_INST(float)
+AMH_MISC_INST(double)
+
+}  // namespace amh

@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads and exports every symbol amh.h declares;
+argument checks that need no GPU return AMH_EINVAL."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2211_03193_gb300 import build, _amh
+    build.build()
+    return _amh.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "amh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amh_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("amh_init", "amh_energy", "amh_sweep", "amh_grad", "amh_get_state",
+                 "amh_set_state", "amh_noisy_restart", "amh_last_error", "amh_destroy"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_has_the_same_names(lib):
+    from paper_2211_03193_gb300 import _amh
+    for name in declared_functions():
+        assert callable(getattr(_amh, name)), name
+
+
+def _init(lib, **over):
+    from paper_2211_03193_gb300 import _amh
+    L = np.array([over.get("L", 8)], dtype=np.int32)
+    ch = np.array([over.get("chains", 2)], dtype=np.int32)
+    B = over.get("B", 5)
+    edges = np.asarray(over.get("edges", 2.0 + np.arange(B + 1)), dtype=np.float64)
+    rows = int(L[0]) * (int(L[0]) - 1) // 2
+    table = np.full((max(rows, 1), max(B, 1)), 1.0 / max(B, 1))
+    tors = np.zeros(int(ch[0]) * 2 * max(int(L[0]), 1), dtype=np.float32)
+    opt = _amh.amh_options_default(**over.get("opt", {}))
+    h = ctypes.c_void_p()
+    st = lib.amh_init(ctypes.byref(h), 1, L.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), tors.ctypes.data,
+                      table.ctypes.data, edges.ctypes.data, B, ctypes.byref(opt))
+    return st, h
+
+
+@pytest.mark.parametrize("over", [
+    dict(B=1),
+    dict(L=1),
+    dict(chains=0),
+    dict(edges=[2.0, 3.0, 3.5, 5.0, 6.0, 7.0]),     # uneven centres
+    dict(edges=[2.0, 3.0, 2.5, 5.0, 6.0, 7.0]),     # not ascending
+    dict(opt=dict(precision=16)),
+    dict(opt=dict(chains_per_cta=3)),
+    dict(opt=dict(threads_per_cta=96)),
+])
+def test_bad_arguments_are_refused_before_any_device_work(lib, over):
+    st, h = _init(lib, **over)
+    assert st == 1  # AMH_EINVAL
+    assert not h.value
+    assert lib.amh_last_error(None)
+
+
+def test_null_context_calls_return_estate(lib):
+    assert lib.amh_energy(None, None) == 5
+    assert lib.amh_sweep(None, 1, 0, 1.0, 0.1, 10, 1, None) == 5
+    lib.amh_destroy(None)

@@ -1,0 +1,355 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every case uses seeded synthetic inputs from ``synth``; expected values come
+only from ``oracle``.  FP32 runs are compared teacher-forced: the oracle
+replays each traced chain adopting the GPU's decisions, recomputes every
+Delta-E in FP64 and checks the GPU's value and decision against it.
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2211_03193_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DEG = math.pi / 180
+
+
+@pytest.fixture(scope="module")
+def amh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_03193_gb300 import build, _amh, sampler
+    build.build()
+    _amh.load()
+    return sampler
+
+
+def f64(x):
+    return np.asarray(x, dtype=np.float64)
+
+
+# Tolerance of an FP32 Delta-E against the FP64 oracle: FP32 pair terms of
+# magnitude up to |E|max carry relative rounding 2^-24 each, and FP32
+# coordinates (after up to resync_every rigid rotations) carry an error of
+# order 1e-5 A, times the slope of the term (at most |E|max per bin width).
+def de_tol(npairs, emax, w):
+    return 1e-6 + npairs * emax * (4 * 2.0 ** -24 + 2e-5 / w)
+
+
+def replay_and_compare(orc, prot, s0, tr, mode, window, T, sigma, t0, seed, chain, fp64):
+    """Teacher-forced replay of one traced GPU chain; returns diagnostics."""
+    P = orc.Problem(prot.L, prot.p, prot.edges)
+    steps = tr.shape[0]
+    forced = tr["accept"].astype(np.uint8)
+    s_end, _, otr = P.run(f64(s0), mode, window, T, sigma, t0, steps, seed, chain,
+                          trace=True, forced=forced)
+    assert np.array_equal(otr["k"], tr["k"])
+    emax = float(np.max(-np.log(np.maximum(prot.p, 1e-300))))
+    w = float(prot.edges[1] - prot.edges[0])
+    k = tr["k"]
+    p = (k + 1) // 2
+    if mode == orc.GLOBAL:
+        npairs = p * (prot.L - p)
+    else:
+        h = window // 2
+        c = k // 2
+        lo = np.maximum(0, c - h)
+        hi = np.minimum(prot.L - 1, c + h)
+        npairs = np.where((p > lo) & (p <= hi), (p - lo) * (hi - p + 1), 0)
+    dE_err = np.abs(tr["dE"] - otr["dV"])
+    if fp64:
+        tol = 1e-9 * (1 + np.abs(otr["dV"]))
+        lnu_tol = 1e-12
+    else:
+        tol = de_tol(npairs, emax, w)
+        lnu_tol = 2e-6
+    assert np.all(np.abs(tr["lnu"] - otr["lnu"]) <= lnu_tol * (1 + np.abs(otr["lnu"])))
+    th_err = np.abs(np.angle(np.exp(1j * (tr["theta_new"] - otr["theta_new"]))))
+    assert np.all(th_err <= (1e-12 if fp64 else 2e-6)), th_err.max()
+    bad = dE_err > tol
+    assert not bad.any(), (np.flatnonzero(bad)[:5], dE_err[bad][:5], tol[bad][:5] if np.ndim(tol) else tol)
+    margin = np.abs(otr["lnu"] + otr["dV"] / T)
+    disagree = tr["accept"] != otr["accept"]
+    allowed = margin <= (tol / T + 1e-5)
+    assert np.all(allowed[disagree]), (np.flatnonzero(disagree & ~allowed)[:5])
+    return dict(max_dE_err=float(dE_err.max()), disagree=int(disagree.sum()), n=steps,
+                s_end=s_end)
+
+
+# ---------------------------------------------------------------- RNG
+def test_philox_bit_exact_with_oracle_and_curand(amh, orc, tmp_path):
+    from paper_2211_03193_gb300 import _amh
+    cases = [(0, 0, 0, 0), (12345, 7, 1 << 33, 0), (2 ** 64 - 1, 2 ** 32 - 1, 2 ** 40 + 5, 1),
+             (987654321987, 1023, 99, 2)]
+    nvcc = os.environ.get("NVCC", "nvcc")
+    so = str(tmp_path / "curand_ref.so")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                    "-Xcompiler", "-fPIC", "-o", so,
+                    os.path.join(ROOT, "tests", "cuda", "curand_philox_ref.cu")], check=True)
+    ref = ctypes.CDLL(so)
+    for seed, chain, t0, stream in cases:
+        words, z, u = _amh.amh_philox(seed, chain, t0, stream, 257)
+        ctr = np.zeros((257, 4), np.uint32)
+        key = np.zeros((257, 2), np.uint32)
+        for i in range(257):
+            t = t0 + i
+            ctr[i] = (chain, t & 0xFFFFFFFF, (t >> 32) & 0xFFFFFFFF, stream)
+            key[i] = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+            want = orc.philox(ctr[i], key[i])
+            assert np.array_equal(words[i], want), (seed, chain, t, words[i], want)
+            _, zo, uo = orc.draw(seed, chain, t, stream)
+            assert float(u[i]) == uo  # 23-bit uniforms are exact in binary32
+            assert abs(float(z[i]) - zo) <= 4e-6 * (1 + abs(zo))
+        out = np.zeros((257, 4), np.uint32)
+        assert ref.curand_philox_ref(ctr.ctypes.data, key.ctypes.data, out.ctypes.data, 257) == 0
+        assert np.array_equal(out, words)
+
+
+# ---------------------------------------------------------------- energy
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("L,chains,C", [(2, 3, 8), (5, 9, 4), (37, 17, 8), (64, 8, 2), (64, 3, 1)])
+def test_energy_matches_oracle(amh, orc, precision, L, chains, C):
+    if precision == 64 and C == 8:
+        C = 4
+    prot = synth.make_protein(L, seed=100 + L)
+    tors = synth.random_torsions(chains, L, seed=L)
+    with amh.Sampler(prot, chains, tors, precision=precision, chains_per_cta=C) as s:
+        E = s.energy()
+        P = orc.Problem(L, prot.p, prot.edges)
+        want = P.energies(f64(tors))
+        rel = 1e-5 if precision == 32 else 1e-12
+        assert np.all(np.abs(E - want) <= rel * np.abs(want) + 1e-9), (E, want)
+        th, E2, bE, bt = s.state()
+        assert np.array_equal(th.reshape(chains, -1), tors)
+        assert np.array_equal(bE, E)
+
+
+def test_energy_uneven_proteins_and_64_bins(amh, orc):
+    Ls = [3, 20, 41, 9]
+    edges = synth.edges_uniform_64()
+    prots = [synth.make_protein(L, edges=edges, sigma_d=1.5, seed=200 + L) for L in Ls]
+    chains = [5, 1, 10, 3]
+    tors = np.concatenate([synth.random_torsions(c, p.L, seed=c + p.L).ravel()
+                           for p, c in zip(prots, chains)])
+    with amh.Sampler(prots, chains, tors, chains_per_cta=4) as s:
+        E = s.energy()
+    want = []
+    off = 0
+    for p, c in zip(prots, chains):
+        P = orc.Problem(p.L, p.p, p.edges)
+        want.append(P.energies(f64(tors[off:off + c * p.n])))
+        off += c * p.n
+    want = np.concatenate(want)
+    assert np.allclose(E, want, rtol=1e-5, atol=1e-9)
+
+
+# ---------------------------------------------------------------- global sweeps
+@pytest.mark.parametrize("precision,C", [(64, 1), (64, 4), (32, 8), (32, 2), (32, 1)])
+def test_global_sweeps_teacher_forced(amh, orc, precision, C):
+    L, chains = 33, 11
+    prot = synth.make_protein(L, seed=300)
+    tors = synth.random_torsions(chains, L, seed=301)
+    n = 2 * L
+    steps = 3 * n + 7  # ragged: ends mid-sweep, with an odd leftover
+    T, sigma, seed = 0.8, 25 * DEG, 99
+    with amh.Sampler(prot, chains, tors, precision=precision, chains_per_cta=C,
+                     trace_chains=chains, trace_capacity=steps, resync_every=50) as s:
+        acc = s.sweep(1, 0, T, sigma, steps, seed)
+        th, E, bE, bt = s.state()
+        for c in range(chains):
+            tr = s.trace(c)
+            assert tr.shape[0] == steps
+            assert acc[c] == tr["accept"].sum()
+            d = replay_and_compare(orc, prot, tors[c], tr, orc.GLOBAL, 0, T, sigma, 0, seed, c,
+                                   precision == 64)
+            if precision == 64:
+                assert d["disagree"] == 0
+                assert np.allclose(th.reshape(chains, -1)[c], d["s_end"], atol=1e-6)
+            # the energy after the call is a fresh FP64 resync of the final state
+            P = orc.Problem(L, prot.p, prot.edges)
+            e_want = P.energy(f64(th.reshape(chains, -1)[c]))
+            assert abs(E[c] - e_want) <= (1e-12 if precision == 64 else 1e-5) * abs(e_want)
+        assert np.all(bE <= E + 1e-9)
+
+
+def test_global_fp64_untouched_trajectory_equals_oracle(amh, orc):
+    """FP64 GPU vs oracle without teacher forcing: identical decisions."""
+    L = 24
+    prot = synth.make_protein(L, seed=310)
+    tors = synth.random_torsions(2, L, seed=311)
+    steps = 5 * 2 * L
+    with amh.Sampler(prot, 2, tors, precision=64, trace_chains=2, trace_capacity=steps) as s:
+        s.sweep(1, 0, 0.5, 15 * DEG, steps, 5)
+        th = s.torsions()
+        P = orc.Problem(L, prot.p, prot.edges)
+        for c in range(2):
+            tr = s.trace(c)
+            send, acc, otr = P.run(f64(tors[c]), orc.GLOBAL, 0, 0.5, 15 * DEG, 0, steps, 5, c,
+                                   trace=True)
+            margin = np.abs(otr["lnu"] + otr["dV"] / 0.5)
+            diff = np.flatnonzero(tr["accept"] != otr["accept"])
+            if diff.size:  # only a near-tie may flip a decision (then paths part)
+                assert margin[diff[0]] < 1e-5
+            else:
+                assert np.allclose(th[c], send, atol=1e-6)
+
+
+def test_split_calls_equal_one_call(amh):
+    L, chains = 40, 8
+    prot = synth.make_protein(L, seed=320)
+    tors = synth.random_torsions(chains, L, seed=321)
+    outs = []
+    for split in ([170], [33, 1, 136], [80, 90]):
+        with amh.Sampler(prot, chains, tors, chains_per_cta=8) as s:
+            for st in split:
+                s.sweep(1, 0, 0.6, 0.3, st, 7)
+            outs.append(s.state()[0])
+            assert s.counter(3) == 170
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_dead_torsions_always_accepted(amh):
+    L = 10
+    prot = synth.make_protein(L, seed=330)
+    tors = synth.random_torsions(4, L, seed=331)
+    with amh.Sampler(prot, 4, tors, trace_chains=4, trace_capacity=2 * 2 * L) as s:
+        s.sweep(1, 0, 1e-6, 0.5, 2 * 2 * L, 3)
+        for c in range(4):
+            tr = s.trace(c)
+            dead = (tr["k"] == 0) | (tr["k"] == 2 * L - 1)
+            assert np.all(tr["accept"][dead] == 1) and np.all(tr["dE"][dead] == 0)
+
+
+# ---------------------------------------------------------------- local sweeps
+@pytest.mark.parametrize("precision,window", [(64, 8), (32, 8), (32, 10), (32, 5), (32, 0),
+                                              (32, 3)])
+def test_local_sweeps_teacher_forced(amh, orc, precision, window):
+    L, chains = 29, 6
+    prot = synth.make_protein(L, seed=400)
+    tors = synth.random_torsions(chains, L, seed=401)
+    n = 2 * L
+    steps = 2 * n
+    T, sigma, seed = 0.3, 20 * DEG, 17
+    with amh.Sampler(prot, chains, tors, precision=precision, trace_chains=chains,
+                     trace_capacity=steps) as s:
+        acc = s.sweep(0, window, T, sigma, steps, seed)
+        th = s.torsions()
+        for c in range(chains):
+            tr = s.trace(c)
+            assert tr.shape[0] == steps and acc[c] == tr["accept"].sum()
+            d = replay_and_compare(orc, prot, tors[c], tr, orc.LOCAL, window, T, sigma, 0, seed,
+                                   c, precision == 64)
+            if precision == 64:
+                assert d["disagree"] == 0
+                assert np.allclose(th[c], d["s_end"], atol=1e-6)
+
+
+def test_local_full_window_equals_global_fp64(amh):
+    """d >= 2n: a local sweep is a global sweep (same visits, same draws)."""
+    L = 8
+    prot = synth.make_protein(L, seed=410)
+    tors = synth.random_torsions(3, L, seed=411)
+    res = []
+    for mode, window in ((1, 0), (0, 2 * 2 * L)):
+        with amh.Sampler(prot, 3, tors, precision=64) as s:
+            s.sweep(mode, window, 0.7, 0.35, 4 * 2 * L, 21)
+            res.append(s.torsions())
+    assert np.allclose(res[0], res[1], atol=1e-9)
+
+
+def test_local_requires_whole_sweeps(amh):
+    from paper_2211_03193_gb300._amh import AmhError
+    prot = synth.make_protein(6, seed=420)
+    with amh.Sampler(prot, 2, synth.random_torsions(2, 6, seed=1)) as s:
+        with pytest.raises(AmhError):
+            s.sweep(0, 8, 1.0, 0.1, 5, 1)
+        s.sweep(1, 0, 1.0, 0.1, 5, 1)
+        with pytest.raises(AmhError):
+            s.sweep(0, 8, 1.0, 0.1, 12, 1)
+        with pytest.raises(AmhError):
+            s.sweep(0, 66, 1.0, 0.1, 12, 1)
+
+
+# ---------------------------------------------------------------- gradient
+@pytest.mark.parametrize("precision", [32, 64])
+def test_grad_matches_oracle(amh, orc, precision):
+    import torch
+    L, batch = 45, 6
+    prot = synth.make_protein(L, seed=500)
+    tors = synth.random_torsions(batch, L, seed=501)
+    dt = torch.float32 if precision == 32 else torch.float64
+    with amh.Sampler(prot, 1, tors[:1], precision=precision) as s:
+        th = torch.tensor(tors, dtype=dt, device="cuda")
+        E, g = s.grad(0, th)
+        E, g = E.cpu().numpy(), g.cpu().numpy()
+    P = orc.Problem(L, prot.p, prot.edges)
+    for b in range(batch):
+        Vo, go = P.grad(f64(tors[b]))
+        if precision == 32:
+            assert abs(E[b] - Vo) <= 1e-5 * abs(Vo)
+            assert np.linalg.norm(g[b] - go) <= 1e-3 * np.linalg.norm(go)
+        else:
+            assert abs(E[b] - Vo) <= 1e-11 * abs(Vo)
+            assert np.linalg.norm(g[b] - go) <= 1e-9 * np.linalg.norm(go)
+        assert g[b][0] == 0 and g[b][-1] == 0
+
+
+# ---------------------------------------------------------------- noisy restart
+def test_noisy_restart_matches_oracle(amh, orc):
+    L, chains = 12, 5
+    prot = synth.make_protein(L, seed=600)
+    tors = synth.random_torsions(chains, L, seed=601)
+    with amh.Sampler(prot, chains, tors, precision=64) as s:
+        s.noisy_restart(30 * DEG, 77)
+        th = s.torsions()
+        E = s.state()[1]
+    P = orc.Problem(L, prot.p, prot.edges)
+    for c in range(chains):
+        want = orc.noisy_restart(f64(tors[c]), 30 * DEG, 77, c)
+        assert np.allclose(th[c], want, atol=2e-7)  # FP32 interface rounding
+        assert abs(E[c] - P.energy(f64(th[c]))) <= 1e-10 * abs(E[c])
+
+
+# ---------------------------------------------------------------- sampler law
+def test_global_mh_on_gpu_samples_exact_boltzmann(amh, orc):
+    """Lattice toy (L=4, K=4): the GPU's global MH visits states with
+    frequency exp(-V/T)/Z (Eq. 1), Z by enumeration with the oracle."""
+    import itertools
+    L, K = 4, 4
+    prot = synth.make_protein(L, seed=21)
+    P = orc.Problem(L, prot.p, prot.edges)
+    n = 2 * L
+    q = 2 * np.pi / K
+    live = list(range(1, n - 1))
+    grid = np.array(list(itertools.product(range(K), repeat=len(live))))
+    S = np.zeros((grid.shape[0], n))
+    S[:, live] = np.angle(np.exp(1j * grid * q))
+    E = P.energies(S)
+    T = float(np.std(E))
+    w = np.exp(-(E - E.min()) / T)
+    pi = w / w.sum()
+    chains = 4096
+    tors = np.zeros((chains, n), np.float32)
+    with amh.Sampler(prot, chains, tors, precision=64, lattice_K=K) as s:
+        s.sweep(1, 0, T, 1.2, 40 * n, 3)  # burn-in
+        counts = np.zeros(K ** len(live))
+        for rep in range(150):
+            s.sweep(1, 0, T, 1.2, n, 3)
+            th = s.torsions()
+            m = np.mod(np.rint(th[:, live] / q).astype(np.int64), K)
+            idx = (m * K ** np.arange(len(live) - 1, -1, -1)).sum(1)
+            counts += np.bincount(idx, minlength=K ** len(live))
+    gidx = (np.mod(grid, K) * K ** np.arange(len(live) - 1, -1, -1)).sum(1)
+    pi_sorted = pi[np.argsort(gidx)]
+    hist = counts / counts.sum()
+    tv = 0.5 * np.abs(hist - pi_sorted).sum()
+    tv_noise = 0.5 * np.sum(np.sqrt(2 * pi_sorted * (1 - pi_sorted) / (np.pi * counts.sum())))
+    assert tv < 1.5 * tv_noise, (tv, tv_noise)
