@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chains-per-cta", type=int, default=0,
+                    help="global-sweep chains per CTA (0 = autotuned)")
+    ap.add_argument("--threads", type=int, default=0, help="global-sweep threads per CTA")
     return ap.parse_args()
 
 
@@ -249,7 +252,8 @@ def run_ours(args):
                               seed=w["seed"])
     tors = synth.random_torsions(chains, L, seed=w["start_seed"] + 1000 * rank)
     stream = torch.cuda.Stream()
-    samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream)
+    samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
+                   chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads)
     C, thr = samp.launch_config()
     sched = schedule_for(w, seed=1 + rank)
     cyc = w["cycle"]

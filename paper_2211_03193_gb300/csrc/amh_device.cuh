@@ -324,4 +324,16 @@ struct GroupDev {
   int pad;
 };
 
+// Allow a kernel to use all dynamic shared memory the device offers on top of
+// its static shared memory.
+template <class K>
+inline cudaError_t allow_dynamic_smem(K kernel, size_t optin) {
+  cudaFuncAttributes at;
+  cudaError_t e = cudaFuncGetAttributes(&at, kernel);
+  if (e != cudaSuccess) return e;
+  const size_t stat = at.sharedSizeBytes;
+  const size_t dyn = optin > stat ? optin - stat : 0;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 }  // namespace amh

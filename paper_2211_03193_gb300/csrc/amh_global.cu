@@ -501,12 +501,10 @@ size_t global_smem_bytes(int Lmax, int nmax, int threads) {
 }
 
 template <class R, int C>
-cudaError_t global_set_smem(size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(global_kernel<R, C>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t global_set_smem(size_t optin) {
+  cudaError_t e = allow_dynamic_smem(global_kernel<R, C>, optin);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(energy_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  return allow_dynamic_smem(energy_kernel<R, C>, optin);
 }
 
 template <class R, int C>

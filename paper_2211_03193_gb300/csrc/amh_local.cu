@@ -184,9 +184,8 @@ size_t local_smem_bytes(int nmax, int chains_per_cta, int threads, int window) {
 }
 
 template <class R>
-cudaError_t local_set_smem(size_t bytes) {
-  return cudaFuncSetAttribute(local_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+cudaError_t local_set_smem(size_t optin) {
+  return allow_dynamic_smem(local_kernel<R>, optin);
 }
 
 template <class R>

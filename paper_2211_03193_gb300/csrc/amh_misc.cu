@@ -201,8 +201,8 @@ cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R
                         double* E_out, R* grad, Tab<R> tab, Geom<R> geom, cudaStream_t st) {
   (void)protein;
   const size_t sm = (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1);
-  cudaError_t e =
-      cudaFuncSetAttribute(grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
   if (e != cudaSuccess) return e;
   if (batch <= 0) return cudaSuccess;
   grad_kernel<R><<<batch, 256, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab, geom);
