@@ -58,7 +58,9 @@ typedef struct {
                               FP64 every this many proposals (default 1000). */
   int chains_per_cta;      /* chains that share one CTA in global sweeps:
                               0 = autotuned at first use, else 1, 2, 4 or 8. */
-  int threads_per_cta;     /* 0 = default (256 for global sweeps). */
+  int threads_per_cta;     /* global sweeps: 0 = autotuned with chains_per_cta
+                              (256 if chains_per_cta is set), else 128, 256
+                              or 512. */
   int trace_chains;        /* record every proposal of chains [0, trace_chains) */
   long long trace_capacity;/* records kept per traced chain (visit order) */
   int lattice_K;           /* test mode: 0 = off; K > 0 snaps proposals to a

@@ -123,7 +123,7 @@ Geom<R> make_geom() {
 template <class R>
 Tab<R> make_tab(const amh_ctx* ctx) {
   Tab<R> t;
-  t.E = (const R*)ctx->table;
+  t.E = (const typename Vec2<R>::T*)ctx->table;
   t.inv_w = (R)(1.0 / ctx->w);
   t.off = (R)(-ctx->c0 / ctx->w);
   t.umax = (R)(ctx->B - 1);
@@ -312,7 +312,7 @@ amh_status check_err_flag(amh_ctx* ctx) {
 template <class R>
 amh_status autotune(amh_ctx* ctx) {
   const int cand_C[4] = {1, 2, 4, 8};
-  const int cand_T[2] = {128, 256};
+  const int cand_T[2] = {256, 512};
   long long* t_scr = nullptr;
   R* th_scr = nullptr;
   R* bt_scr = nullptr;
@@ -392,7 +392,7 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   // table: p (or -ln p) -> padded R rows, via a temporary FP64 copy
   double* tmp = nullptr;
   const size_t tbytes = sizeof(double) * (size_t)ctx->rows_total * ctx->B;
-  CK(ctx, cudaMalloc(&ctx->table, sizeof(R) * (size_t)ctx->rows_total * ctx->Bp + 64));
+  CK(ctx, cudaMalloc(&ctx->table, 2 * sizeof(R) * (size_t)ctx->rows_total * ctx->Bp + 64));
   CK(ctx, cudaMalloc(&tmp, std::max<size_t>(tbytes, 8)));
   CK(ctx, cudaMemcpy(tmp, table, tbytes, cudaMemcpyHostToDevice));
   CK(ctx, launch_prep_table<R>(tmp, ctx->rows_total, ctx->B, ctx->Bp, ctx->opt.table_is_neglog,
@@ -529,8 +529,9 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
     return set_err(nullptr, AMH_EINVAL, "chains_per_cta must be 0, 1, 2, 4 or 8");
   if (o.precision == 64 && o.chains_per_cta == 8)
     return set_err(nullptr, AMH_EINVAL, "precision 64 allows at most 4 chains per CTA");
-  if (o.threads_per_cta != 0 && o.threads_per_cta != 128 && o.threads_per_cta != 256)
-    return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 128 or 256");
+  if (o.threads_per_cta != 0 && o.threads_per_cta != 128 && o.threads_per_cta != 256 &&
+      o.threads_per_cta != 512)
+    return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 128, 256 or 512");
   if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)
     return set_err(nullptr, AMH_EINVAL, "negative option");
   // bins: evenly spaced centres
@@ -556,7 +557,7 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   ctx->precision = o.precision;
   ctx->stream = (cudaStream_t)o.stream;
   ctx->B = B;
-  ctx->Bp = ((B + 1) + 3) & ~3;
+  ctx->Bp = (B + 1) & ~1;  // (value, slope) entries per row: even, so rows are 16-byte aligned
   ctx->c0 = cen[0];
   ctx->w = w;
   ctx->nprot = n_proteins;

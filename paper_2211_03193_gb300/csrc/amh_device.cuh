@@ -56,10 +56,11 @@ __device__ __forceinline__ V3<R> unit(V3<R> a) {
   return a * rsqrt_(dot(a, a));
 }
 
-// Euclidean distance.  FP32: d2 * rsqrt(d2) (one MUFU op); FP64: sqrt.
+// Euclidean distance.  FP32: d2 * rsqrt(d2) (one MUFU op), with 1e-30
+// folded into the first FMA so coincident points give 0, not NaN; FP64: sqrt.
 __device__ __forceinline__ float dist_(V3<float> a, V3<float> b) {
-  V3<float> d = a - b;
-  float d2 = fmaxf(dot(d, d), 1e-30f);
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const float d2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, 1e-30f)));
   return d2 * rsqrtf(d2);
 }
 __device__ __forceinline__ double dist_(V3<double> a, V3<double> b) {
@@ -186,41 +187,64 @@ __device__ __forceinline__ Aff<R> identity_map() {
 
 // ------------------------------------------------------------------ table
 // Pair term of Eq. 5: -ln p interpolated linearly between evenly spaced bin
-// centres c_j = c0 + j w, flat outside [c_0, c_{B-1}].  Rows are padded to
-// Bp >= B+1 entries with copies of the last value, so j = B-1 reads a
-// valid neighbour.
+// centres c_j = c0 + j w, flat outside [c_0, c_{B-1}].  Each row stores, per
+// bin, the pair (E_j, E_{j+1} - E_j) so one 8-byte load and one FMA give the
+// term; the last bin and the padding hold (E_{B-1}, 0).
 template <class R>
-struct Tab {
-  const R* __restrict__ E;  // [rows][Bp]
-  R inv_w;                  // 1 / w
-  R off;                    // -c0 / w
-  R umax;                   // B - 1
-  int Bp;
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using T = float2;
+};
+template <>
+struct Vec2<double> {
+  using T = double2;
 };
 
 template <class R>
-__device__ __forceinline__ R pair_term(const R* __restrict__ row, R d, const Tab<R>& tb) {
+struct Tab {
+  const typename Vec2<R>::T* __restrict__ E;  // [rows][Bp] (value, slope per bin)
+  R inv_w;                                    // 1 / w
+  R off;                                      // -c0 / w
+  R umax;                                     // B - 1
+  int Bp;
+};
+
+// floor(u) for 0 <= u < 2^22 as (integer, float): adding 2^23 rounded down
+// leaves floor(u) in the low mantissa bits (FP32 pipe only).
+__device__ __forceinline__ int floor_small(float u, float* jf) {
+  const float f = __fadd_rd(u, 8388608.0f);
+  *jf = f - 8388608.0f;
+  return __float_as_int(f) - 0x4B000000;
+}
+__device__ __forceinline__ int floor_small(double u, double* jf) {
+  const int j = (int)u;
+  *jf = (double)j;
+  return j;
+}
+
+template <class R>
+__device__ __forceinline__ R pair_term(const typename Vec2<R>::T* __restrict__ row, R d,
+                                       const Tab<R>& tb) {
   R u = fma(d, tb.inv_w, tb.off);
   u = fmin(fmax(u, R(0)), tb.umax);
-  int j = (int)u;
-  R t = u - (R)j;
-  R e0 = __ldg(row + j);
-  R e1 = __ldg(row + j + 1);
-  return fma(t, e1 - e0, e0);
+  R jf;
+  const int j = floor_small(u, &jf);
+  const typename Vec2<R>::T v = __ldg(row + j);
+  return fma(u - jf, v.y, v.x);
 }
 
 // Value and slope d e / d d (zero on the flat ends).
 template <class R>
-__device__ __forceinline__ R pair_term_slope(const R* __restrict__ row, R d, const Tab<R>& tb,
-                                             R* slope) {
-  R u0 = fma(d, tb.inv_w, tb.off);
-  R u = fmin(fmax(u0, R(0)), tb.umax);
-  int j = (int)u;
-  R t = u - (R)j;
-  R e0 = __ldg(row + j);
-  R e1 = __ldg(row + j + 1);
-  *slope = (u0 >= R(0) && u0 < tb.umax) ? (e1 - e0) * tb.inv_w : R(0);
-  return fma(t, e1 - e0, e0);
+__device__ __forceinline__ R pair_term_slope(const typename Vec2<R>::T* __restrict__ row, R d,
+                                             const Tab<R>& tb, R* slope) {
+  const R u0 = fma(d, tb.inv_w, tb.off);
+  const R u = fmin(fmax(u0, R(0)), tb.umax);
+  R jf;
+  const int j = floor_small(u, &jf);
+  const typename Vec2<R>::T v = __ldg(row + j);
+  *slope = (u0 >= R(0) && u0 < tb.umax) ? v.y * tb.inv_w : R(0);
+  return fma(u - jf, v.y, v.x);
 }
 
 // Row r(a,b) = a L - a(a+1)/2 + (b-a-1), a < b.

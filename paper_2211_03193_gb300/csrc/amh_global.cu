@@ -153,7 +153,7 @@ __device__ void full_energy(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, i
     const int b1 = min(L, b0 + kFC);
     if (b0 >= b1) continue;
     const V3<R> xa = s.cb(a, c);
-    const R* row = tb.E + tab_off + (long long)row_of(L, a, b0) * tb.Bp;
+    const auto* row = tb.E + tab_off + (long long)row_of(L, a, b0) * tb.Bp;
     typename AccT<R>::T part = 0;
     for (int b = b0; b < b1; ++b, row += tb.Bp) part += pair_term(row, dist_(xa, s.cb(b, c)), tb);
     acc += (double)part;
@@ -221,10 +221,11 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
       y21 = apply(A21, xm);
     }
     const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
+#pragma unroll 4
     for (int f = fb; f < fe; ++f) {
       const V3<R> xf = s.cb(f, c);
       const int ra = min(f, m), rb = max(f, m);
-      const R* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
+      const auto* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
       const R e0 = pair_term(row, dist_(xf, xm), tb);
       const R e1 = pair_term(row, dist_(xf, y1), tb);
       acc1 += e1 - e0;
@@ -452,7 +453,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
 }
 
 template <class R, int C>
-__global__ void __launch_bounds__(256) global_kernel(SweepArgs<R> a) {
+__global__ void __launch_bounds__(512) global_kernel(SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_group;
   const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(256) global_kernel(SweepArgs<R> a) {
 }
 
 template <class R, int C>
-__global__ void __launch_bounds__(256) energy_kernel(SweepArgs<R> a) {
+__global__ void __launch_bounds__(512) energy_kernel(SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_group;
   const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);

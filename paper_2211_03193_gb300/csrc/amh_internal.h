@@ -68,7 +68,8 @@ cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R
                         int batch, double* E_out, R* grad, Tab<R> tab, Geom<R> geom,
                         cudaStream_t st);
 
-// Table preparation: p (or -ln p) float64 -> padded R rows.
+// Table preparation: p (or -ln p) float64 -> padded rows of (value, slope)
+// pairs of R (out points at rows * Bp pairs).
 template <class R>
 cudaError_t launch_prep_table(const double* p, long long rows, int B, int Bp, int neglog, R* out,
                               cudaStream_t st);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
             }
             const Aff<R> A = rotation(Pax, Qax, wrap_angle(thn - th));
             typename AccT<R>::T acc = 0;
-            const R* tab = a.tab.E + P.tab_off;
+            const auto* tab = a.tab.E + P.tab_off;
             for (int b = p; b <= hi; ++b) {
               const int jb = b - lo;
               const V3<R> xb = v3<R>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                 const V3<R> xa = v3<R>(cbs[(ja * 3 + 0) * nt + tid],
                                        cbs[(ja * 3 + 1) * nt + tid],
                                        cbs[(ja * 3 + 2) * nt + tid]);
-                const R* row = tab + (long long)row_of(L, aa, b) * a.tab.Bp;
+                const auto* row = tab + (long long)row_of(L, aa, b) * a.tab.Bp;
                 acc += pair_term(row, dist_(xa, yb), a.tab) - pair_term(row, dist_(xa, xb), a.tab);
               }
             }

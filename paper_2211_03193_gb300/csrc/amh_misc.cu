@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, con
       if (a == b) continue;
       const V3<R> xa = v3<R>(CB[3 * a], CB[3 * a + 1], CB[3 * a + 2]);
       const int ra = min(a, b), rb = max(a, b);
-      const R* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
+      const auto* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
       const V3<R> dlt = xb - xa;
       const R d = sqrt(dot(dlt, dlt));
       R sl;
@@ -113,18 +113,27 @@ __global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, con
 }
 
 // ---------------------------------------------------------------- table
+// Entry j of a row: (E_j, E_{j+1} - E_j) with E = -ln max(p, 1e-300); the
+// last bin and the padding hold (E_{B-1}, 0).
+__device__ __forceinline__ double neglog_p(double q, int neglog) {
+  return neglog ? q : -log(q > 1e-300 ? q : 1e-300);
+}
+
 template <class R>
 __global__ void prep_table_kernel(const double* __restrict__ p, long long rows, int B, int Bp,
-                                  int neglog, R* __restrict__ out) {
+                                  int neglog, typename Vec2<R>::T* __restrict__ out) {
   const long long total = rows * Bp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long r = i / Bp;
-    int j = (int)(i - r * Bp);
-    if (j >= B) j = B - 1;  // padding repeats the last bin
-    double q = p[r * B + j];
-    double e = neglog ? q : -log(q > 1e-300 ? q : 1e-300);
-    out[i] = (R)e;
+    const int j = (int)(i - r * Bp);
+    const double* pr = p + r * B;
+    const double e0 = neglog_p(pr[j < B ? j : B - 1], neglog);
+    const double e1 = j + 1 < B ? neglog_p(pr[j + 1], neglog) : e0;
+    typename Vec2<R>::T v;
+    v.x = (R)e0;
+    v.y = (R)(e1 - e0);
+    out[i] = v;
   }
 }
 
@@ -213,7 +222,8 @@ template <class R>
 cudaError_t launch_prep_table(const double* p, long long rows, int B, int Bp, int neglog, R* out,
                               cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  prep_table_kernel<R><<<grid_for(rows * Bp, 256), 256, 0, st>>>(p, rows, B, Bp, neglog, out);
+  prep_table_kernel<R><<<grid_for(rows * Bp, 256), 256, 0, st>>>(
+      p, rows, B, Bp, neglog, reinterpret_cast<typename Vec2<R>::T*>(out));
   return cudaGetLastError();
 }
 
