@@ -127,6 +127,8 @@ Tab<R> make_tab(const amh_ctx* ctx) {
   t.inv_w = (R)(1.0 / ctx->w);
   t.off = (R)(-ctx->c0 / ctx->w);
   t.umax = (R)(ctx->B - 1);
+  t.k1 = (R)(1.0 / ctx->w / (ctx->B - 1));
+  t.k2 = (R)(-ctx->c0 / ctx->w / (ctx->B - 1));
   t.Bp = ctx->Bp;
   return t;
 }

@@ -56,12 +56,20 @@ __device__ __forceinline__ V3<R> unit(V3<R> a) {
   return a * rsqrt_(dot(a, a));
 }
 
+// 1/sqrt(x) by the approximate MUFU instruction with denormals flushed
+// (x >= 1e-30 here, so no denormal path is needed).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Euclidean distance.  FP32: d2 * rsqrt(d2) (one MUFU op), with 1e-30
 // folded into the first FMA so coincident points give 0, not NaN; FP64: sqrt.
 __device__ __forceinline__ float dist_(V3<float> a, V3<float> b) {
   const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   const float d2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, 1e-30f)));
-  return d2 * rsqrtf(d2);
+  return d2 * rsqrt_ftz(d2);
 }
 __device__ __forceinline__ double dist_(V3<double> a, V3<double> b) {
   V3<double> d = a - b;
@@ -207,6 +215,7 @@ struct Tab {
   R inv_w;                                    // 1 / w
   R off;                                      // -c0 / w
   R umax;                                     // B - 1
+  R k1, k2;                                   // inv_w / umax, off / umax
   int Bp;
 };
 
@@ -223,15 +232,33 @@ __device__ __forceinline__ int floor_small(double u, double* jf) {
   return j;
 }
 
-template <class R>
-__device__ __forceinline__ R pair_term(const typename Vec2<R>::T* __restrict__ row, R d,
-                                       const Tab<R>& tb) {
-  R u = fma(d, tb.inv_w, tb.off);
-  u = fmin(fmax(u, R(0)), tb.umax);
-  R jf;
+__device__ __forceinline__ double pair_term(const double2* __restrict__ row, double d,
+                                            const Tab<double>& tb) {
+  double u = fma(d, tb.inv_w, tb.off);
+  u = fmin(fmax(u, 0.0), tb.umax);
+  double jf;
   const int j = floor_small(u, &jf);
-  const typename Vec2<R>::T v = __ldg(row + j);
+  const double2 v = __ldg(row + j);
   return fma(u - jf, v.y, v.x);
+}
+
+// FP32: the bin coordinate u = (d - c0)/w clamped to [0, B-1] is
+// umax * sat(d k1 + k2) (one FFMA.SAT); floor(u) + 2^23 comes from one FMA
+// rounded down, whose bit pattern also indexes the entry: bin j sits at
+// byte 8 j of the row, i.e. at row - 8 * 0x4B000000 + 8 * bits.
+__device__ __forceinline__ float pair_term(const float2* __restrict__ row, float d,
+                                           const Tab<float>& tb) {
+  const float us = __saturatef(fmaf(d, tb.k1, tb.k2));
+  const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
+  const float t = fmaf(us, tb.umax, 8388608.0f - f);
+  const char* base = reinterpret_cast<const char*>(row) - 8ull * 0x4B000000u;
+  float2 v;
+  // one wide multiply-add forms the entry address from the float's bits
+  asm("{\n\t.reg .u64 ad;\n\tmad.wide.u32 ad, %2, 8, %3;\n\t"
+      "ld.global.nc.v2.f32 {%0, %1}, [ad];\n\t}"
+      : "=f"(v.x), "=f"(v.y)
+      : "r"((unsigned)__float_as_int(f)), "l"(base));
+  return fmaf(t, v.y, v.x);
 }
 
 // Value and slope d e / d d (zero on the flat ends).

@@ -221,11 +221,16 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
       y21 = apply(A21, xm);
     }
     const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
-#pragma unroll 4
+    // rows of the pairs (f, m): contiguous in f when m < f; when f < m,
+    // r(f+1, m) - r(f, m) = L - f - 2
+    const bool mfirst = m < fb;
+    const auto* row =
+        tb.E + tab_off + (long long)(mfirst ? row_of(L, m, fb) : row_of(L, fb, m)) * tb.Bp;
+    int step = mfirst ? 1 : L - fb - 2;
+    const int dstep = mfirst ? 0 : -1;
+#pragma unroll 2
     for (int f = fb; f < fe; ++f) {
       const V3<R> xf = s.cb(f, c);
-      const int ra = min(f, m), rb = max(f, m);
-      const auto* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
       const R e0 = pair_term(row, dist_(xf, xm), tb);
       const R e1 = pair_term(row, dist_(xf, y1), tb);
       acc1 += e1 - e0;
@@ -235,6 +240,8 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
         acc2 += e2 - e0;
         acc21 += e21 - e1;
       }
+      row += (long long)step * tb.Bp;
+      step += dstep;
     }
   }
   reduce3(s, (double)acc1, (double)acc2, (double)acc21);
