@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--chains-per-cta", type=int, default=0,
                     help="global-sweep chains per CTA (0 = autotuned)")
     ap.add_argument("--threads", type=int, default=0, help="global-sweep threads per CTA")
+    ap.add_argument("--stage", type=int, default=0,
+                    help="table rows: 0 tuned, 1 staged in shared memory, 2 through L1")
     return ap.parse_args()
 
 
@@ -253,8 +255,9 @@ def run_ours(args):
     tors = synth.random_torsions(chains, L, seed=w["start_seed"] + 1000 * rank)
     stream = torch.cuda.Stream()
     samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
-                   chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads)
-    C, thr = samp.launch_config()
+                   chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
+                   stage_table=args.stage)
+    C, thr, D = samp.launch_config()
     sched = schedule_for(w, seed=1 + rank)
     cyc = w["cycle"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -351,7 +354,9 @@ def run_ours(args):
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": achieved / peak_tf, "traffic": None,
-            "kernel": "global_kernel<float,%d> (global sweep, %d threads/CTA)" % (C, thr),
+            "kernel": "global_kernel<float,%d,%s> (global sweep, %d threads/CTA%s)" % (
+                C, "true" if D else "false", thr,
+                ", table rows staged %d deep" % D if D else ", table rows through L1"),
             "launch_ms": g_ms, "pair_evals_per_launch": evals_glob_launch,
             "flop_per_eval": FLOP_PER_EVAL,
             "peak_basis": "%d SMs x %d FP32 lanes x 2 (FMA) x %.0f MHz (%s max clock)" % (
@@ -364,7 +369,7 @@ def run_ours(args):
                       "T 2.0->0.05, sigma 10->4 deg over %d sweeps" % w["total_sweeps"],
                       "proposals_per_step_per_gpu": props_step, "l2": "flushed between steps "
                       "(256 MB write); table 6.6 MB is L2-resident within a step",
-                      "chains_per_cta": C, "threads_per_cta": thr,
+                      "chains_per_cta": C, "threads_per_cta": thr, "stage_depth": D,
                       "parallelism": "independent chains per GPU (replicas)"},
            "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
            "roofline": roof, "gpu_launches": args.steps * (cyc + 1),

@@ -42,7 +42,7 @@ typedef enum {
   AMH_EINVAL = 1,   /* bad argument; nothing was done */
   AMH_ENOMEM = 2,   /* device allocation failed */
   AMH_ECUDA = 3,    /* CUDA runtime error (context is now broken) */
-  AMH_ETIMEOUT = 4, /* a bounded device wait gave up (reserved) */
+  AMH_ETIMEOUT = 4, /* a bounded device wait (shared-memory staging) gave up */
   AMH_ESTATE = 5    /* context broken by an earlier error, or NULL */
 } amh_status;
 
@@ -67,6 +67,12 @@ typedef struct {
                               K-point lattice, s' = q round((s + sigma z)/q),
                               q = 2 pi / K (symmetric proposal). */
   int table_is_neglog;     /* 0: table holds p; 1: table already holds -ln p */
+  int stage_table;         /* global sweeps read the straddle block's table rows
+                              0: as tuned (staged in shared memory by bulk
+                              async copies when it fits), 1: always staged
+                              (AMH_EINVAL if impossible: needs precision 32
+                              and 4 or 8 chains per CTA), 2: never staged
+                              (read through the L1 cache). */
   void* stream;            /* cudaStream_t; NULL = the legacy default stream */
 } amh_options;
 
@@ -202,8 +208,10 @@ amh_status amh_philox(unsigned long long seed, unsigned chain, unsigned long lon
 /* Text of the last error of ctx (or of the last context-free call). */
 const char* amh_last_error(const amh_ctx* ctx);
 
-/* Chains per CTA and threads per CTA the global sweeps use (after tuning). */
-amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta);
+/* Launch shape of the global sweeps (after tuning): chains per CTA, threads
+ * per CTA and staging-ring depth (0 = table rows read through L1). */
+amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta,
+                             int* stage_depth);
 
 /* Free everything the context owns.  NULL is ignored. */
 void amh_destroy(amh_ctx* ctx);

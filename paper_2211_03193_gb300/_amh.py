@@ -32,7 +32,7 @@ class amh_options(ctypes.Structure):
                 ("chains_per_cta", ctypes.c_int), ("threads_per_cta", ctypes.c_int),
                 ("trace_chains", ctypes.c_int), ("trace_capacity", ctypes.c_longlong),
                 ("lattice_K", ctypes.c_int), ("table_is_neglog", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stage_table", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class amh_trace_rec(ctypes.Structure):
@@ -74,7 +74,7 @@ def load() -> ctypes.CDLL:
                              ctypes.c_longlong, vp, vp, vp]
     L.amh_last_error.argtypes = [vp]
     L.amh_last_error.restype = ctypes.c_char_p
-    L.amh_launch_config.argtypes = [vp, ip, ip]
+    L.amh_launch_config.argtypes = [vp, ip, ip, ip]
     L.amh_destroy.argtypes = [vp]
     L.amh_destroy.restype = None
     for name in ("amh_init", "amh_energy", "amh_sweep", "amh_sweeps", "amh_grad", "amh_get_state",
@@ -194,9 +194,9 @@ def amh_philox(seed, chain, t0, stream, count):
 
 
 def amh_launch_config(ctx):
-    c, t = ctypes.c_int(), ctypes.c_int()
-    _check(load().amh_launch_config(ctx, ctypes.byref(c), ctypes.byref(t)), ctx)
-    return c.value, t.value
+    c, t, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().amh_launch_config(ctx, ctypes.byref(c), ctypes.byref(t), ctypes.byref(d)), ctx)
+    return c.value, t.value, d.value
 
 
 def amh_last_error(ctx=None) -> str:

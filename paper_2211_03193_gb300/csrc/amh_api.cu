@@ -49,6 +49,7 @@ struct amh_ctx {
   long long* trace_count = nullptr;
   // launch configuration
   int C = 8, threads = 256, grid_global = 1;
+  int stage_depth = 0;  // > 0: global sweeps stage table rows through shared memory
   int sm_count = 1;
   size_t smem_optin = 0;
   std::string msg;
@@ -56,6 +57,9 @@ struct amh_ctx {
 };
 
 namespace {
+
+// room left for the kernels' static shared memory when sizing dynamic smem
+constexpr size_t kStaticSmemMargin = 1024;
 
 thread_local std::string g_free_error;
 
@@ -158,81 +162,104 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   a.trace_cap = ctx->opt.trace_capacity;
   a.trace_count = ctx->trace_count;
   a.err = ctx->err;
+  a.stage_depth = ctx->stage_depth;
   return a;
 }
 
-// ---- dispatch over (precision, C) ------------------------------------------
+// ---- dispatch over (precision, C, staging) ---------------------------------
+int row_bytes(const amh_ctx* ctx) { return ctx->Bp * (ctx->precision == 64 ? 16 : 8); }
+
 template <class R>
-size_t gsmem(int C, int Lmax, int nmax, int threads) {
+size_t gsmem(int C, int Lmax, int nmax, int threads, int D, int RB) {
   switch (C) {
-    case 1: return global_smem_bytes<R, 1>(Lmax, nmax, threads);
-    case 2: return global_smem_bytes<R, 2>(Lmax, nmax, threads);
-    case 4: return global_smem_bytes<R, 4>(Lmax, nmax, threads);
-    default: return global_smem_bytes<R, 8>(Lmax, nmax, threads);
+    case 1: return global_smem_bytes<R, 1>(Lmax, nmax, threads, D, RB);
+    case 2: return global_smem_bytes<R, 2>(Lmax, nmax, threads, D, RB);
+    case 4: return global_smem_bytes<R, 4>(Lmax, nmax, threads, D, RB);
+    default: return global_smem_bytes<R, 8>(Lmax, nmax, threads, D, RB);
   }
 }
 template <>
-size_t gsmem<double>(int C, int Lmax, int nmax, int threads) {
+size_t gsmem<double>(int C, int Lmax, int nmax, int threads, int D, int RB) {
   switch (C) {
-    case 1: return global_smem_bytes<double, 1>(Lmax, nmax, threads);
-    case 2: return global_smem_bytes<double, 2>(Lmax, nmax, threads);
-    default: return global_smem_bytes<double, 4>(Lmax, nmax, threads);
+    case 1: return global_smem_bytes<double, 1>(Lmax, nmax, threads, D, RB);
+    case 2: return global_smem_bytes<double, 2>(Lmax, nmax, threads, D, RB);
+    default: return global_smem_bytes<double, 4>(Lmax, nmax, threads, D, RB);
   }
 }
 
 template <class R>
 cudaError_t gset(int C, size_t bytes) {
+  cudaError_t e = cudaSuccess;
   switch (C) {
-    case 1: return global_set_smem<R, 1>(bytes);
-    case 2: return global_set_smem<R, 2>(bytes);
-    case 4: return global_set_smem<R, 4>(bytes);
-    default: return global_set_smem<R, 8>(bytes);
+    case 1: return global_set_smem<R, 1, false>(bytes);
+    case 2: return global_set_smem<R, 2, false>(bytes);
+    case 4:
+      e = global_set_smem<R, 4, false>(bytes);
+      return e != cudaSuccess ? e : global_set_smem<R, 4, true>(bytes);
+    default:
+      e = global_set_smem<R, 8, false>(bytes);
+      return e != cudaSuccess ? e : global_set_smem<R, 8, true>(bytes);
   }
 }
 template <>
 cudaError_t gset<double>(int C, size_t bytes) {
   switch (C) {
-    case 1: return global_set_smem<double, 1>(bytes);
-    case 2: return global_set_smem<double, 2>(bytes);
-    default: return global_set_smem<double, 4>(bytes);
+    case 1: return global_set_smem<double, 1, false>(bytes);
+    case 2: return global_set_smem<double, 2, false>(bytes);
+    default: return global_set_smem<double, 4, false>(bytes);
   }
 }
 
 template <class R>
-cudaError_t gocc(int C, int threads, size_t sm, int* per_sm) {
+cudaError_t gocc(int C, bool ST, int threads, size_t sm, int* per_sm) {
   switch (C) {
-    case 1: return global_occupancy<R, 1>(threads, sm, per_sm);
-    case 2: return global_occupancy<R, 2>(threads, sm, per_sm);
-    case 4: return global_occupancy<R, 4>(threads, sm, per_sm);
-    default: return global_occupancy<R, 8>(threads, sm, per_sm);
+    case 1: return global_occupancy<R, 1, false>(threads, sm, per_sm);
+    case 2: return global_occupancy<R, 2, false>(threads, sm, per_sm);
+    case 4: return ST ? global_occupancy<R, 4, true>(threads, sm, per_sm)
+                      : global_occupancy<R, 4, false>(threads, sm, per_sm);
+    default: return ST ? global_occupancy<R, 8, true>(threads, sm, per_sm)
+                       : global_occupancy<R, 8, false>(threads, sm, per_sm);
   }
 }
 template <>
-cudaError_t gocc<double>(int C, int threads, size_t sm, int* per_sm) {
+cudaError_t gocc<double>(int C, bool ST, int threads, size_t sm, int* per_sm) {
+  (void)ST;
   switch (C) {
-    case 1: return global_occupancy<double, 1>(threads, sm, per_sm);
-    case 2: return global_occupancy<double, 2>(threads, sm, per_sm);
-    default: return global_occupancy<double, 4>(threads, sm, per_sm);
+    case 1: return global_occupancy<double, 1, false>(threads, sm, per_sm);
+    case 2: return global_occupancy<double, 2, false>(threads, sm, per_sm);
+    default: return global_occupancy<double, 4, false>(threads, sm, per_sm);
   }
 }
 
 template <class R>
-cudaError_t glaunch(bool energy, int C, const SweepArgs<R>& a, int threads, int grid,
+cudaError_t glaunch(bool energy, int C, bool ST, const SweepArgs<R>& a, int threads, int grid,
                     cudaStream_t st) {
   switch (C) {
-    case 1: return energy ? launch_energy<R, 1>(a, threads, grid, st) : launch_global<R, 1>(a, threads, grid, st);
-    case 2: return energy ? launch_energy<R, 2>(a, threads, grid, st) : launch_global<R, 2>(a, threads, grid, st);
-    case 4: return energy ? launch_energy<R, 4>(a, threads, grid, st) : launch_global<R, 4>(a, threads, grid, st);
-    default: return energy ? launch_energy<R, 8>(a, threads, grid, st) : launch_global<R, 8>(a, threads, grid, st);
+    case 1: return energy ? launch_energy<R, 1>(a, threads, grid, st)
+                          : launch_global<R, 1, false>(a, threads, grid, st);
+    case 2: return energy ? launch_energy<R, 2>(a, threads, grid, st)
+                          : launch_global<R, 2, false>(a, threads, grid, st);
+    case 4:
+      if (energy) return launch_energy<R, 4>(a, threads, grid, st);
+      return ST ? launch_global<R, 4, true>(a, threads, grid, st)
+                : launch_global<R, 4, false>(a, threads, grid, st);
+    default:
+      if (energy) return launch_energy<R, 8>(a, threads, grid, st);
+      return ST ? launch_global<R, 8, true>(a, threads, grid, st)
+                : launch_global<R, 8, false>(a, threads, grid, st);
   }
 }
 template <>
-cudaError_t glaunch<double>(bool energy, int C, const SweepArgs<double>& a, int threads, int grid,
-                            cudaStream_t st) {
+cudaError_t glaunch<double>(bool energy, int C, bool ST, const SweepArgs<double>& a, int threads,
+                            int grid, cudaStream_t st) {
+  (void)ST;
   switch (C) {
-    case 1: return energy ? launch_energy<double, 1>(a, threads, grid, st) : launch_global<double, 1>(a, threads, grid, st);
-    case 2: return energy ? launch_energy<double, 2>(a, threads, grid, st) : launch_global<double, 2>(a, threads, grid, st);
-    default: return energy ? launch_energy<double, 4>(a, threads, grid, st) : launch_global<double, 4>(a, threads, grid, st);
+    case 1: return energy ? launch_energy<double, 1>(a, threads, grid, st)
+                          : launch_global<double, 1, false>(a, threads, grid, st);
+    case 2: return energy ? launch_energy<double, 2>(a, threads, grid, st)
+                          : launch_global<double, 2, false>(a, threads, grid, st);
+    default: return energy ? launch_energy<double, 4>(a, threads, grid, st)
+                           : launch_global<double, 4, false>(a, threads, grid, st);
   }
 }
 
@@ -270,17 +297,29 @@ amh_status upload_groups(amh_ctx* ctx, const std::vector<GroupDev>& g, GroupDev*
   return AMH_OK;
 }
 
+// Deepest staging ring (slots per warp, 2..4) that fits, or 0.  Staging
+// exists for FP32 with 4 or 8 chains per CTA.
+int stage_depth_for(const amh_ctx* ctx, int C, int threads) {
+  if (ctx->precision != 32 || (C != 4 && C != 8)) return 0;
+  for (int D = 4; D >= 2; --D)
+    if (gsmem<float>(C, ctx->Lmax, ctx->nmax, threads, D, row_bytes(ctx)) <= ctx->smem_optin - kStaticSmemMargin)
+      return D;
+  return 0;
+}
+
 template <class R>
-amh_status configure_global(amh_ctx* ctx, int C, int threads) {
-  const size_t sm = gsmem<R>(C, ctx->Lmax, ctx->nmax, threads);
-  if (sm > ctx->smem_optin) return set_err(ctx, AMH_EINVAL, "shared memory for this C does not fit");
+amh_status configure_global(amh_ctx* ctx, int C, int threads, int D) {
+  const size_t sm = gsmem<R>(C, ctx->Lmax, ctx->nmax, threads, D, D ? row_bytes(ctx) : 0);
+  if (sm > ctx->smem_optin - kStaticSmemMargin)
+    return set_err(ctx, AMH_EINVAL, "shared memory for this C does not fit");
   amh_status st = upload_groups(ctx, make_groups(ctx, C), &ctx->ggroups_d, &ctx->nggroups);
   if (st) return st;
   ctx->C = C;
   ctx->threads = threads;
+  ctx->stage_depth = D;
   // persistent grid: as many CTAs as are resident at once, at most one per group
   int per_sm = 1;
-  CK(ctx, gocc<R>(C, threads, sm, &per_sm));
+  CK(ctx, gocc<R>(C, D > 0, threads, sm, &per_sm));
   ctx->grid_global = std::max(1, std::min(ctx->nggroups, ctx->sm_count * std::max(per_sm, 1)));
   return AMH_OK;
 }
@@ -289,7 +328,7 @@ template <class R>
 amh_status run_energy(amh_ctx* ctx) {
   SweepArgs<R> a = make_args<R>(ctx);
   CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
-  CK(ctx, glaunch<R>(true, ctx->C, a, ctx->threads, ctx->grid_global, ctx->stream));
+  CK(ctx, glaunch<R>(true, ctx->C, false, a, ctx->threads, ctx->grid_global, ctx->stream));
   return AMH_OK;
 }
 
@@ -305,6 +344,7 @@ amh_status check_err_flag(amh_ctx* ctx) {
   int h = 0;
   CK(ctx, cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h & 2) return set_err(ctx, AMH_ETIMEOUT, "a shared-memory staging wait gave up");
   if (h) return set_err(ctx, AMH_ECUDA, "device reported a non-finite energy");
   return AMH_OK;
 }
@@ -329,7 +369,7 @@ amh_status autotune(amh_ctx* ctx) {
   CK(ctx, cudaEventCreate(&e0));
   CK(ctx, cudaEventCreate(&e1));
   float best_ms = 1e30f;
-  int bestC = 0, bestT = 256;
+  int bestC = 0, bestT = 256, bestD = 0;
   const long long steps = 64;
   std::vector<long long> tstart(ctx->total_chains);
   for (int p = 0; p < ctx->nprot; ++p)
@@ -338,8 +378,15 @@ amh_status autotune(amh_ctx* ctx) {
   for (int C : cand_C) {
     if (C > max_C(ctx->precision)) continue;
     for (int T : cand_T) {
-      if (gsmem<R>(C, ctx->Lmax, ctx->nmax, T) > ctx->smem_optin) continue;
-      amh_status st = configure_global<R>(ctx, C, T);
+     for (int staged = 0; staged < 2; ++staged) {
+      if (staged && ctx->opt.stage_table == 2) continue;
+      if (!staged && ctx->opt.stage_table == 1) continue;
+      const int D = staged ? stage_depth_for(ctx, C, T) : 0;
+      if (staged && D == 0) continue;
+      if (gsmem<R>(C, ctx->Lmax, ctx->nmax, T, D, D ? row_bytes(ctx) : 0) >
+          ctx->smem_optin - kStaticSmemMargin)
+        continue;
+      amh_status st = configure_global<R>(ctx, C, T, D);
       if (st) return st;
       float ms_sum = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
@@ -364,7 +411,7 @@ amh_status autotune(amh_ctx* ctx) {
         a.resync_every = 1 << 30;
         CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
         CK(ctx, cudaEventRecord(e0, ctx->stream));
-        CK(ctx, glaunch<R>(false, C, a, T, ctx->grid_global, ctx->stream));
+        CK(ctx, glaunch<R>(false, C, D > 0, a, T, ctx->grid_global, ctx->stream));
         CK(ctx, cudaEventRecord(e1, ctx->stream));
         CK(ctx, cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -375,7 +422,9 @@ amh_status autotune(amh_ctx* ctx) {
         best_ms = ms_sum;
         bestC = C;
         bestT = T;
+        bestD = D;
       }
+     }
     }
   }
   cudaEventDestroy(e0);
@@ -386,7 +435,9 @@ amh_status autotune(amh_ctx* ctx) {
   cudaFree(e_scr);
   cudaFree(be_scr);
   if (!bestC) return set_err(ctx, AMH_EINVAL, "no launch shape fits in shared memory");
-  return configure_global<R>(ctx, bestC, bestT);
+  amh_status st = check_err_flag(ctx);
+  if (st) return st;
+  return configure_global<R>(ctx, bestC, bestT, bestD);
 }
 
 template <class R>
@@ -417,8 +468,12 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   if (ctx->opt.chains_per_cta == 0) {
     st = autotune<R>(ctx);
   } else {
+    const int C = ctx->opt.chains_per_cta;
     const int T = ctx->opt.threads_per_cta ? ctx->opt.threads_per_cta : 256;
-    st = configure_global<R>(ctx, ctx->opt.chains_per_cta, T);
+    const int D = ctx->opt.stage_table == 2 ? 0 : stage_depth_for(ctx, C, T);
+    if (ctx->opt.stage_table == 1 && D == 0)
+      return set_err(ctx, AMH_EINVAL, "table staging needs FP32, 4 or 8 chains per CTA and room");
+    st = configure_global<R>(ctx, C, T, D);
   }
   if (st) return st;
   // local groups for every chains-per-CTA option
@@ -445,7 +500,8 @@ amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma
   a.window = window;
   CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
   if (mode == AMH_GLOBAL) {
-    CK(ctx, glaunch<R>(false, ctx->C, a, ctx->threads, ctx->grid_global, ctx->stream));
+    CK(ctx, glaunch<R>(false, ctx->C, ctx->stage_depth > 0, a, ctx->threads, ctx->grid_global,
+                       ctx->stream));
   } else {
     const int h = window / 2;
     const int ncol = std::max(4 * h, 1);
@@ -455,11 +511,12 @@ amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma
     const int Gc = 1 << q;
     int threads = 256;
     size_t sm = local_smem_bytes<R>(ctx->nmax, Gc, threads, window);
-    while (sm > ctx->smem_optin && threads > 32) {
+    while (sm > ctx->smem_optin - kStaticSmemMargin && threads > 32) {
       threads /= 2;
       sm = local_smem_bytes<R>(ctx->nmax, Gc, threads, window);
     }
-    if (sm > ctx->smem_optin) return set_err(ctx, AMH_EINVAL, "window too large for shared memory");
+    if (sm > ctx->smem_optin - kStaticSmemMargin)
+      return set_err(ctx, AMH_EINVAL, "window too large for shared memory");
     a.groups = ctx->lgroups_d[q];
     a.ngroups = ctx->nlgroups[q];
     const int per_sm = std::max(1, std::min((int)(ctx->smem_optin / std::max<size_t>(sm, 1)),
@@ -507,6 +564,7 @@ void amh_options_default(amh_options* opt) {
   opt->trace_capacity = 0;
   opt->lattice_K = 0;
   opt->table_is_neglog = 0;
+  opt->stage_table = 0;
   opt->stream = nullptr;
 }
 
@@ -534,6 +592,8 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   if (o.threads_per_cta != 0 && o.threads_per_cta != 128 && o.threads_per_cta != 256 &&
       o.threads_per_cta != 512)
     return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 128, 256 or 512");
+  if (o.stage_table < 0 || o.stage_table > 2)
+    return set_err(nullptr, AMH_EINVAL, "stage_table must be 0, 1 or 2");
   if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)
     return set_err(nullptr, AMH_EINVAL, "negative option");
   // bins: evenly spaced centres
@@ -872,10 +932,12 @@ const char* amh_last_error(const amh_ctx* ctx) {
   return ctx ? ctx->msg.c_str() : g_free_error.c_str();
 }
 
-amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta) {
+amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta,
+                             int* stage_depth) {
   if (!ctx) return AMH_ESTATE;
   if (chains_per_cta) *chains_per_cta = ctx->C;
   if (threads_per_cta) *threads_per_cta = ctx->threads;
+  if (stage_depth) *stage_depth = ctx->stage_depth;
   return AMH_OK;
 }
 

@@ -274,6 +274,70 @@ __device__ __forceinline__ R pair_term_slope(const typename Vec2<R>::T* __restri
   return fma(u - jf, v.y, v.x);
 }
 
+// The same term read from a row staged in shared memory (32-bit address:
+// one multiply-add forms the entry address).
+__device__ __forceinline__ float pair_term_smem(uint32_t row, float d, const Tab<float>& tb) {
+  const float us = __saturatef(fmaf(d, tb.k1, tb.k2));
+  const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
+  const float t = fmaf(us, tb.umax, 8388608.0f - f);
+  const uint32_t ad = row - 8u * 0x4B000000u + 8u * (uint32_t)__float_as_int(f);
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(ad));
+  return fmaf(t, v.y, v.x);
+}
+
+// ------------------------------------------------------------------ async copies
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier: gives up (false) after
+// 2^24 tries or about 2^31 clock cycles (~1 s), whichever comes first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (int i = 0; i < (1 << 24); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > (1ll << 31)) break;
+  }
+  return false;
+}
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, both ends 16-byte aligned) from
+// global to this CTA's shared memory, completing on mbarrier `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 // Row r(a,b) = a L - a(a+1)/2 + (b-a-1), a < b.
 __device__ __forceinline__ int row_of(int L, int a, int b) {
   return a * L - ((a * (a + 1)) >> 1) + (b - a - 1);

@@ -34,8 +34,10 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cbx, cby, cbz, maps, part, ecur, thn, lnu, acc, commit, flag, total;
-  __host__ __device__ Layout(int Lmax, int nmax, int W) {
+  size_t theta, bb, cbx, cby, cbz, maps, part, ecur, thn, lnu, acc, commit, flag, bars, ring,
+      total;
+  // D ring slots per warp of 32/C rows of RB bytes (D = 0: no staging)
+  __host__ __device__ Layout(int Lmax, int nmax, int W, int D = 0, int RB = 0) {
     size_t o = 0;
     theta = o; o = align16(o + sizeof(R) * (size_t)nmax * C);
     bb = o;    o = align16(o + sizeof(R) * (size_t)Lmax * 9 * C);
@@ -50,6 +52,9 @@ struct Layout {
     acc = o;   o = align16(o + sizeof(long long) * C);
     commit = o; o = align16(o + sizeof(int) * C);
     flag = o;  o = align16(o + sizeof(int) * C);
+    bars = o;  o = align16(o + sizeof(unsigned long long) * (size_t)W * D);
+    o = (o + 127) & ~size_t(127);
+    ring = o;  o = align16(o + (size_t)W * D * (32 / C) * RB);
     total = o;
   }
 };
@@ -69,6 +74,8 @@ struct Shm {
   long long* acc;
   int* commit;
   int* flag;
+  unsigned long long* bars;  // [W][D] mbarriers of the staging rings
+  unsigned char* ring;       // [W][D][32/C][RB] staged table rows
   __device__ Shm(unsigned char* base, const Layout<R, C>& l) {
     theta = (R*)(base + l.theta);
     bb = (R*)(base + l.bb);
@@ -83,6 +90,8 @@ struct Shm {
     acc = (long long*)(base + l.acc);
     commit = (int*)(base + l.commit);
     flag = (int*)(base + l.flag);
+    bars = (unsigned long long*)(base + l.bars);
+    ring = base + l.ring;
   }
   __device__ V3<R> cb(int i, int c) const {
     return v3<R>(cbx[i * C + c], cby[i * C + c], cbz[i * C + c]);
@@ -247,6 +256,147 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
   reduce3(s, (double)acc1, (double)acc2, (double)acc21);
 }
 
+// The straddle block with its table rows staged in shared memory.  Each warp
+// owns a ring of D slots; a slot holds the S = 32/C rows (one per slice) of
+// one pair-iteration and completes on its own mbarrier.  Work items are
+// (group of S moving atoms, chunk of fixed atoms): slice s takes moving
+// atom m = group + s and all slices of a warp walk the same fixed atoms, so
+// the warp's control flow is uniform.  A fetch cursor runs D iterations
+// ahead of the compute cursor; lane 0 of each slice issues the bulk copy of
+// its row.  Returns false (after flagging) if a wait gave up.
+struct RowCursor {
+  int it, f, fe, mb;   // item, fixed atom, end of chunk, first moving atom of the group
+  const float2* row;   // this lane's row (f, mb + slice)
+  int step, dstep;
+  bool valid;
+};
+
+template <int C>
+__device__ __forceinline__ void cursor_setup(RowCursor& k, int it, int items, int nch, int m0,
+                                             int m1, int f0, int f1, int L, int sl,
+                                             const float2* tab, int Bp) {
+  constexpr int S = 32 / C;
+  k.it = it;
+  k.valid = it < items;
+  if (!k.valid) return;
+  const int g = it / nch, ch = it - g * nch;
+  k.mb = m0 + g * S;
+  k.f = f0 + ch * kFC;
+  k.fe = min(k.f + kFC, f1);
+  const int m = k.mb + sl;
+  if (m < m1) {
+    const bool mfirst = m < k.f;
+    k.row = tab + (long long)(mfirst ? row_of(L, m, k.f) : row_of(L, k.f, m)) * Bp;
+    k.step = mfirst ? 1 : L - k.f - 2;
+    k.dstep = mfirst ? 0 : -1;
+  }
+}
+
+template <int C, bool FUSED>
+__device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long long tab_off, int L,
+                                  int m0, int m1, int f0, int f1, int D, unsigned& par,
+                                  int* err) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  constexpr int S = 32 / C;
+  const int c = lane % C, sl = lane / C;
+  const int Bp = tb.Bp;
+  const int RB = Bp * (int)sizeof(float2);
+  const float2* tab = tb.E + tab_off;
+  Aff<float> A1, A2, A21;
+  load_aff<float, C>(s.maps + 36 * c, A1);
+  if (FUSED) {
+    load_aff<float, C>(s.maps + 36 * c + 12, A2);
+    load_aff<float, C>(s.maps + 36 * c + 24, A21);
+  }
+  const int nF = f1 - f0;
+  const int nch = (nF + kFC - 1) / kFC;
+  const int nmg = (m1 - m0 + S - 1) / S;
+  const int items = nmg * nch;
+  const uint32_t ring = smem_addr(s.ring + (size_t)warp * D * S * RB);
+  const uint32_t bar0 = smem_addr(s.bars + (size_t)warp * D);
+
+  RowCursor F;
+  cursor_setup<C>(F, warp, items, nch, m0, m1, f0, f1, L, sl, tab, Bp);
+  int qf = 0;
+  // issue the copies of the fetch cursor's iteration into slot qf % D
+  auto issue = [&]() {
+    const int slot = qf % D;
+    const uint32_t bar = bar0 + 8u * slot;
+    const int nact = min(S, m1 - F.mb);
+    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(nact * RB));
+    __syncwarp();
+    if (c == 0 && F.mb + sl < m1) {
+      fence_proxy_async_smem();
+      bulk_g2s(ring + (uint32_t)((slot * S + sl) * RB), F.row, (unsigned)RB, bar);
+    }
+    ++qf;
+    if (F.f + 1 < F.fe) {
+      ++F.f;
+      F.row += (long long)F.step * Bp;
+      F.step += F.dstep;
+    } else {
+      cursor_setup<C>(F, F.it + W, items, nch, m0, m1, f0, f1, L, sl, tab, Bp);
+    }
+  };
+  for (int d = 0; d < D && F.valid; ++d) issue();
+
+  float acc1 = 0.f, acc2 = 0.f, acc21 = 0.f;
+  int q = 0;
+  bool ok = true;
+  for (int it = warp; it < items && ok; it += W) {
+    const int g = it / nch, ch = it - g * nch;
+    const int m = m0 + g * S + sl;
+    const bool act = m < m1;
+    V3<float> xm = v3<float>(0.f, 0.f, 0.f), y1 = xm, y2 = xm, y21 = xm;
+    if (act) {
+      xm = s.cb(m, c);
+      y1 = apply(A1, xm);
+      if (FUSED) {
+        y2 = apply(A2, xm);
+        y21 = apply(A21, xm);
+      }
+    }
+    const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
+    for (int f = fb; f < fe; ++f) {
+      const int slot = q % D;
+      const bool got = mbar_wait_bounded(bar0 + 8u * slot, (par >> slot) & 1u);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      par ^= 1u << slot;
+      if (act) {
+        const V3<float> xf = s.cb(f, c);
+        const uint32_t srow = ring + (uint32_t)((slot * S + sl) * RB);
+        const float e0 = pair_term_smem(srow, dist_(xf, xm), tb);
+        const float e1 = pair_term_smem(srow, dist_(xf, y1), tb);
+        acc1 += e1 - e0;
+        if (FUSED) {
+          const float e2 = pair_term_smem(srow, dist_(xf, y2), tb);
+          const float e21 = pair_term_smem(srow, dist_(xf, y21), tb);
+          acc2 += e2 - e0;
+          acc21 += e21 - e1;
+        }
+      }
+      __syncwarp();
+      ++q;
+      if (F.valid) issue();
+    }
+  }
+  if (!ok) {
+    // a copy did not arrive: flag it and wait (bounded) for the copies still
+    // in flight before the slots are given up
+    if (lane == 0) atomicOr(err, 2);
+    for (; q < qf; ++q) {
+      const int slot = q % D;
+      mbar_wait_bounded(bar0 + 8u * slot, (par >> slot) & 1u);
+      par ^= 1u << slot;
+    }
+  }
+  reduce3(s, (double)acc1, (double)acc2, (double)acc21);
+  return ok;
+}
+
 // Apply each chain's committed map to its moving residues [m0, m1).
 template <class R, int C>
 __device__ void commit_moves(Shm<R, C>& s, int m0, int m1) {
@@ -332,9 +482,9 @@ __device__ void store_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev&
   }
 }
 
-template <class R, int C>
+template <class R, int C, bool ST>
 __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G,
-                          const ProteinDev& P) {
+                          const ProteinDev& P, unsigned& par, int* abort_flag) {
   const int L = P.L, n = P.n;
   load_group(s, a, G, P);
   const long long t0 = a.tcount[G.chain0];
@@ -413,11 +563,21 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       since += 1;
       continue;
     }
-    if (fused)
-      pair_block<R, C, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
-    else
-      pair_block<R, C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+    if constexpr (ST) {
+      const bool ok =
+          fused ? pair_block_staged<C, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1,
+                                             a.stage_depth, par, a.err)
+                : pair_block_staged<C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1,
+                                              a.stage_depth, par, a.err);
+      if (!ok) *(volatile int*)abort_flag = 1;
+    } else {
+      if (fused)
+        pair_block<R, C, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+      else
+        pair_block<R, C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+    }
     __syncthreads();
+    if (*(volatile int*)abort_flag) break;  // a staging wait gave up: stop (flagged)
     if (threadIdx.x < C) {
       const int c = threadIdx.x;
       const int chain = G.chain0 + c;
@@ -459,21 +619,31 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   store_group(s, a, G, P, t0 + steps, true);
 }
 
-template <class R, int C>
+template <class R, int C, bool ST>
 __global__ void __launch_bounds__(512) global_kernel(SweepArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_group;
-  const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);
+  __shared__ int s_abort;
+  const int W = blockDim.x >> 5;
+  const int D = ST ? a.stage_depth : 0;
+  const Layout<R, C> lay(a.Lmax, a.nmax, W, D, ST ? a.tab.Bp * (int)sizeof(typename Vec2<R>::T) : 0);
   Shm<R, C> s(smem, lay);
+  if (threadIdx.x == 0) s_abort = 0;
+  if (ST && (threadIdx.x & 31) == 0) {
+    const int w = threadIdx.x >> 5;
+    for (int d = 0; d < D; ++d) mbar_init(smem_addr(s.bars + w * D + d), 1u);
+    mbar_init_fence();
+  }
+  unsigned par = 0;  // per warp: phase parity to wait for, one bit per slot
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_group = atomicAdd(a.queue, 1);
+    if (threadIdx.x == 0) s_group = s_abort ? a.ngroups : atomicAdd(a.queue, 1);
     __syncthreads();
     const int g = s_group;
     if (g >= a.ngroups) break;
     const GroupDev G = a.groups[g];
     const ProteinDev P = a.prot[G.protein];
-    run_group(s, a, G, P);
+    run_group<R, C, ST>(s, a, G, P, par, &s_abort);
   }
 }
 
@@ -504,42 +674,50 @@ __global__ void __launch_bounds__(512) energy_kernel(SweepArgs<R> a) {
 }  // namespace
 
 template <class R, int C>
-size_t global_smem_bytes(int Lmax, int nmax, int threads) {
-  return Layout<R, C>(Lmax, nmax, threads / 32).total;
+size_t global_smem_bytes(int Lmax, int nmax, int threads, int stage_depth, int row_bytes) {
+  return Layout<R, C>(Lmax, nmax, threads / 32, stage_depth, row_bytes).total;
 }
 
-template <class R, int C>
+template <class R, int C, bool ST>
 cudaError_t global_set_smem(size_t optin) {
-  cudaError_t e = allow_dynamic_smem(global_kernel<R, C>, optin);
+  cudaError_t e = allow_dynamic_smem(global_kernel<R, C, ST>, optin);
   if (e != cudaSuccess) return e;
   return allow_dynamic_smem(energy_kernel<R, C>, optin);
 }
 
-template <class R, int C>
+template <class R, int C, bool ST>
 cudaError_t global_occupancy(int threads, size_t smem, int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, global_kernel<R, C>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, global_kernel<R, C, ST>, threads,
+                                                       smem);
 }
 
-template <class R, int C>
+template <class R, int C, bool ST>
 cudaError_t launch_global(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st) {
-  const size_t sm = global_smem_bytes<R, C>(a.Lmax, a.nmax, threads);
-  global_kernel<R, C><<<grid, threads, sm, st>>>(a);
+  const int D = ST ? a.stage_depth : 0;
+  const size_t sm = global_smem_bytes<R, C>(a.Lmax, a.nmax, threads, D,
+                                            ST ? a.tab.Bp * (int)sizeof(typename Vec2<R>::T) : 0);
+  global_kernel<R, C, ST><<<grid, threads, sm, st>>>(a);
   return cudaGetLastError();
 }
 
 template <class R, int C>
 cudaError_t launch_energy(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st) {
-  const size_t sm = global_smem_bytes<R, C>(a.Lmax, a.nmax, threads);
+  const size_t sm = global_smem_bytes<R, C>(a.Lmax, a.nmax, threads, 0, 0);
   energy_kernel<R, C><<<grid, threads, sm, st>>>(a);
   return cudaGetLastError();
 }
 
-#define AMH_INST(R, C)                                                                      \
-  template size_t global_smem_bytes<R, C>(int, int, int);                                  \
-  template cudaError_t global_set_smem<R, C>(size_t);                                      \
-  template cudaError_t global_occupancy<R, C>(int, size_t, int*);                          \
-  template cudaError_t launch_global<R, C>(const SweepArgs<R>&, int, int, cudaStream_t);   \
+#define AMH_INST(R, C)                                                                          \
+  template size_t global_smem_bytes<R, C>(int, int, int, int, int);                            \
+  template cudaError_t global_set_smem<R, C, false>(size_t);                                   \
+  template cudaError_t global_occupancy<R, C, false>(int, size_t, int*);                       \
+  template cudaError_t launch_global<R, C, false>(const SweepArgs<R>&, int, int, cudaStream_t); \
   template cudaError_t launch_energy<R, C>(const SweepArgs<R>&, int, int, cudaStream_t);
+#define AMH_INST_ST(C)                                                                          \
+  template cudaError_t global_set_smem<float, C, true>(size_t);                                \
+  template cudaError_t global_occupancy<float, C, true>(int, size_t, int*);                    \
+  template cudaError_t launch_global<float, C, true>(const SweepArgs<float>&, int, int,        \
+                                                     cudaStream_t);
 
 AMH_INST(float, 1)
 AMH_INST(float, 2)
@@ -548,5 +726,7 @@ AMH_INST(float, 8)
 AMH_INST(double, 1)
 AMH_INST(double, 2)
 AMH_INST(double, 4)
+AMH_INST_ST(4)
+AMH_INST_ST(8)
 
 }  // namespace amh

@@ -32,6 +32,7 @@ struct SweepArgs {
   int resync_every;
   int lattice_K;
   int window;           // local sweeps: d
+  int stage_depth;      // global sweeps, staged variant: ring slots per warp
   int Lmax, nmax;       // smem sizing
   TraceRec* trace;
   int trace_chains;
@@ -41,15 +42,18 @@ struct SweepArgs {
 };
 
 // Global sweeps (Eqs. 1-3, Alg. 1 first loop) and full-energy resync.
-template <class R, int C>
+// ST: the straddle-block rows are staged into shared memory by bulk async
+// copies (stage_depth slots per warp of 32/C rows of row_bytes) instead of
+// being read through L1.
+template <class R, int C, bool ST>
 cudaError_t launch_global(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st);
 template <class R, int C>
 cudaError_t launch_energy(const SweepArgs<R>& a, int threads, int grid, cudaStream_t st);
 template <class R, int C>
-size_t global_smem_bytes(int Lmax, int nmax, int threads);
-template <class R, int C>
+size_t global_smem_bytes(int Lmax, int nmax, int threads, int stage_depth, int row_bytes);
+template <class R, int C, bool ST>
 cudaError_t global_set_smem(size_t bytes);
-template <class R, int C>
+template <class R, int C, bool ST>
 cudaError_t global_occupancy(int threads, size_t smem, int* per_sm);
 
 // Local sweeps (Eqs. 4a-b, Eq. 6, Alg. 1 second loop).

@@ -152,8 +152,12 @@ def test_energy_uneven_proteins_and_64_bins(amh, orc):
 
 
 # ---------------------------------------------------------------- global sweeps
-@pytest.mark.parametrize("precision,C", [(64, 1), (64, 4), (32, 8), (32, 2), (32, 1)])
-def test_global_sweeps_teacher_forced(amh, orc, precision, C):
+@pytest.mark.parametrize("precision,C,stage,threads", [
+    (64, 1, 2, 256), (64, 4, 2, 256), (32, 8, 2, 256), (32, 2, 2, 256), (32, 1, 2, 128),
+    (32, 8, 1, 512), (32, 4, 1, 256), (32, 8, 1, 128)])
+def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads):
+    """stage 1: table rows staged in shared memory by bulk async copies;
+    stage 2: read through L1."""
     L, chains = 33, 11
     prot = synth.make_protein(L, seed=300)
     tors = synth.random_torsions(chains, L, seed=301)
@@ -161,7 +165,11 @@ def test_global_sweeps_teacher_forced(amh, orc, precision, C):
     steps = 3 * n + 7  # ragged: ends mid-sweep, with an odd leftover
     T, sigma, seed = 0.8, 25 * DEG, 99
     with amh.Sampler(prot, chains, tors, precision=precision, chains_per_cta=C,
+                     threads_per_cta=threads, stage_table=stage,
                      trace_chains=chains, trace_capacity=steps, resync_every=50) as s:
+        assert s.launch_config()[2] == (0 if stage == 2 else s.launch_config()[2])
+        if stage == 1:
+            assert s.launch_config()[2] >= 2
         acc = s.sweep(1, 0, T, sigma, steps, seed)
         th, E, bE, bt = s.state()
         for c in range(chains):
@@ -208,13 +216,14 @@ def test_global_fp64_untouched_trajectory_equals_oracle(amh, orc):
                 assert np.allclose(th[c], send, atol=1e-6)
 
 
-def test_split_calls_equal_one_call(amh):
+@pytest.mark.parametrize("stage", [1, 2])
+def test_split_calls_equal_one_call(amh, stage):
     L, chains = 40, 8
     prot = synth.make_protein(L, seed=320)
     tors = synth.random_torsions(chains, L, seed=321)
     outs = []
     for split in ([170], [33, 1, 136], [80, 90]):
-        with amh.Sampler(prot, chains, tors, chains_per_cta=8) as s:
+        with amh.Sampler(prot, chains, tors, chains_per_cta=8, stage_table=stage) as s:
             for st in split:
                 s.sweep(1, 0, 0.6, 0.3, st, 7)
             outs.append(s.state()[0])
