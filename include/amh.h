@@ -216,6 +216,38 @@ amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per
 /* Free everything the context owns.  NULL is ignored. */
 void amh_destroy(amh_ctx* ctx);
 
+/*
+ * amh_grad_noalloc -- amh_grad without a context and without allocating.
+ * (The paper has no counterpart: this is a deployment variant.)
+ *
+ * For callers that must not call cudaMalloc: code that runs while a CUDA
+ * graph is being captured (allocation is not a capturable operation), hosts
+ * whose device memory belongs to a pool or caching allocator they do not
+ * control, and services with a fixed device-memory budget.  amh_grad reads a
+ * distogram table that amh_init prepared in device memory the library
+ * allocated; here the table is prepared on every call into one static
+ * device array of AMH_NOALLOC_MAX_ENTRIES (value, slope) entries of 8 bytes
+ * (16 MiB; rows L(L-1)/2 times entries per row (B+1 rounded down to even)
+ * must fit: L <= 332 for 37 bins), which every GPU that loads the library
+ * holds until the process exits.  Larger problems return AMH_EINVAL.
+ *   L, B, edges, table_is_neglog   as in amh_init (edges on the host)
+ *   table       device, float64 [L(L-1)/2][B]: p (or -ln p)
+ *   theta       device, float32 [batch][2 L]
+ *   E_out       device, [batch] doubles;  dE_dtheta  device, float32 [batch][2 L]
+ *   stream      cudaStream_t or NULL
+ * FP32 pair terms as amh_grad at precision 32.  Runs asynchronously on
+ * `stream`; no call allocates or frees memory.  The first call on each
+ * device looks up the device address of the static array (with that device
+ * current); make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (different streams, or different host threads) race and
+ * must be serialised by the caller.  Errors: amh_last_error(NULL).
+ */
+#define AMH_NOALLOC_MAX_ENTRIES (1 << 21)
+amh_status amh_grad_noalloc(int L, int B, const double* table, int table_is_neglog,
+                            const double* edges, const float* theta, int batch, double* E_out,
+                            float* dE_dtheta, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

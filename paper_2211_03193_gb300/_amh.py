@@ -77,9 +77,11 @@ def load() -> ctypes.CDLL:
     L.amh_launch_config.argtypes = [vp, ip, ip, ip]
     L.amh_destroy.argtypes = [vp]
     L.amh_destroy.restype = None
+    L.amh_grad_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp,
+                                   ctypes.c_int, vp, vp, vp]
     for name in ("amh_init", "amh_energy", "amh_sweep", "amh_sweeps", "amh_grad", "amh_get_state",
                  "amh_set_state", "amh_noisy_restart", "amh_get_trace", "amh_counter",
-                 "amh_philox", "amh_launch_config"):
+                 "amh_philox", "amh_launch_config", "amh_grad_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -208,6 +210,19 @@ def amh_destroy(ctx):
         load().amh_destroy(ctx)
 
 
+def amh_grad_noalloc(L, B, table, table_is_neglog, edges, theta, batch, E_out, dE_dtheta,
+                     stream=None):
+    """No-allocation gradient: table/theta/E_out/dE_dtheta are device tensors,
+    edges a host array; see amh.h."""
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(load().amh_grad_noalloc(int(L), int(B), _ptr(table), int(table_is_neglog),
+                                   edges.ctypes.data, _ptr(theta), int(batch), _ptr(E_out),
+                                   _ptr(dE_dtheta), stream), None)
+
+
 EXPORTED = ["amh_options_default", "amh_init", "amh_energy", "amh_sweep", "amh_sweeps",
             "amh_grad", "amh_get_state", "amh_set_state", "amh_noisy_restart", "amh_get_trace",
-            "amh_counter", "amh_philox", "amh_last_error", "amh_launch_config", "amh_destroy"]
+            "amh_counter", "amh_philox", "amh_last_error", "amh_launch_config", "amh_destroy",
+            "amh_grad_noalloc"]

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libamh.so")
 
-SOURCES = ["amh_api.cu", "amh_global.cu", "amh_local.cu", "amh_misc.cu"]
+SOURCES = ["amh_api.cu", "amh_global.cu", "amh_local.cu", "amh_misc.cu", "amh_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]

@@ -101,30 +101,6 @@ bool is_device_ptr(const void* p) {
 }
 
 template <class R>
-Geom<R> make_geom() {
-  const double d2r = 3.14159265358979323846 / 180.0;
-  const double bNCA = 1.458, bCAC = 1.525, bCN = 1.329, bCACB = 1.52;
-  const double aNCAC = 111.2 * d2r, aCACN = 116.2 * d2r, aCNCA = 121.7 * d2r;
-  const double aCCACB = 109.5 * d2r, tCB = 122.6 * d2r;
-  Geom<R> g;
-  g.bNCA = (R)bNCA;
-  g.bCAC = (R)bCAC;
-  g.cosNCAC = (R)std::cos(aNCAC);
-  g.sinNCAC = (R)std::sin(aNCAC);
-  g.pN_c = (R)(-bCN * std::cos(aCACN));
-  g.pN_s = (R)(bCN * std::sin(aCACN));
-  g.pCA_c = (R)(-bNCA * std::cos(aCNCA));
-  g.pCA_s = (R)(bNCA * std::sin(aCNCA));
-  g.pC_c = (R)(-bCAC * std::cos(aNCAC));
-  g.pC_s = (R)(bCAC * std::sin(aNCAC));
-  g.pCB_c = (R)(-bCACB * std::cos(aCCACB));
-  g.pCB_s = (R)(bCACB * std::sin(aCCACB));
-  g.cbT_c = (R)std::cos(tCB);
-  g.cbT_s = (R)std::sin(tCB);
-  return g;
-}
-
-template <class R>
 Tab<R> make_tab(const amh_ctx* ctx) {
   Tab<R> t;
   t.E = (const typename Vec2<R>::T*)ctx->table;
@@ -152,7 +128,7 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   a.best_E = ctx->best_E;
   a.acc_out = ctx->acc;
   a.tab = make_tab<R>(ctx);
-  a.geom = make_geom<R>();
+  a.geom = ideal_geometry<R>();
   a.resync_every = ctx->opt.resync_every;
   a.lattice_K = ctx->opt.lattice_K;
   a.Lmax = ctx->Lmax;
@@ -551,6 +527,10 @@ void free_ctx(amh_ctx* ctx) {
 
 }  // namespace
 
+namespace amh {
+void set_context_free_error(const std::string& m) { g_free_error = m; }
+}  // namespace amh
+
 extern "C" {
 
 void amh_options_default(amh_options* opt) {
@@ -790,11 +770,11 @@ amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, dou
   if (ctx->precision == 64) {
     CK(ctx, launch_grad<double>(&ctx->prot_h[protein], protein, L, (const double*)theta, batch,
                                 E_out, (double*)dE_dtheta, make_tab<double>(ctx),
-                                make_geom<double>(), ctx->stream));
+                                ideal_geometry<double>(), ctx->stream));
   } else {
     CK(ctx, launch_grad<float>(&ctx->prot_h[protein], protein, L, (const float*)theta, batch,
                                E_out, (float*)dE_dtheta, make_tab<float>(ctx),
-                               make_geom<float>(), ctx->stream));
+                               ideal_geometry<float>(), ctx->stream));
   }
   return AMH_OK;
 }

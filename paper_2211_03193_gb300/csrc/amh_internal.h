@@ -2,12 +2,43 @@
 // translation units (not part of the public ABI).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "amh_device.cuh"
 
 namespace amh {
+
+// Ideal geometry of G(s) (bond lengths and angles listed in amh.h) as the
+// (-b cos a, b sin a) pairs the builders use, computed in double precision.
+template <class R>
+inline Geom<R> ideal_geometry() {
+  const double d2r = 3.14159265358979323846 / 180.0;
+  const double bNCA = 1.458, bCAC = 1.525, bCN = 1.329, bCACB = 1.52;
+  const double aNCAC = 111.2 * d2r, aCACN = 116.2 * d2r, aCNCA = 121.7 * d2r;
+  const double aCCACB = 109.5 * d2r, tCB = 122.6 * d2r;
+  Geom<R> g;
+  g.bNCA = (R)bNCA;
+  g.bCAC = (R)bCAC;
+  g.cosNCAC = (R)std::cos(aNCAC);
+  g.sinNCAC = (R)std::sin(aNCAC);
+  g.pN_c = (R)(-bCN * std::cos(aCACN));
+  g.pN_s = (R)(bCN * std::sin(aCACN));
+  g.pCA_c = (R)(-bNCA * std::cos(aCNCA));
+  g.pCA_s = (R)(bNCA * std::sin(aCNCA));
+  g.pC_c = (R)(-bCAC * std::cos(aNCAC));
+  g.pC_s = (R)(bCAC * std::sin(aNCAC));
+  g.pCB_c = (R)(-bCACB * std::cos(aCCACB));
+  g.pCB_s = (R)(bCACB * std::sin(aCCACB));
+  g.cbT_c = (R)std::cos(tCB);
+  g.cbT_s = (R)std::sin(tCB);
+  return g;
+}
+
+// Message returned by amh_last_error(NULL) (calls without a context).
+void set_context_free_error(const std::string& m);
 
 // Arguments of a sweep / energy launch over chain groups.
 template <class R>

@@ -1,0 +1,84 @@
+"""amh_grad_noalloc: the gradient entry point for callers that cannot
+allocate device memory (for example code running while a CUDA graph is
+captured, or hosts whose device memory belongs to an allocator they do not
+control).  Its output must match amh_grad's, call after call, although the
+prepared table now lives in one static device array that every call shares.
+
+Collected last on purpose: if it fails, a run that stops at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2211_03193_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_03193_gb300 import build, _amh, sampler
+    build.build()
+    _amh.load()
+    return torch, _amh, sampler
+
+
+def reference(sampler, prot, theta):
+    """E and dE/dtheta from the existing context path (amh_grad)."""
+    with sampler.Sampler(prot, 1, theta[:1].cpu().numpy()) as s:
+        E, g = s.grad(0, theta)
+        return E.clone(), g.clone()
+
+
+def test_noalloc_matches_amh_grad_on_two_calls_in_a_row(mods):
+    torch, amh, sampler = mods
+    cases = [(57, 6, 700), (33, 9, 701)]  # different proteins: the second call must not
+    for L, batch, seed in cases:          # see the first call's table
+        prot = synth.make_protein(L, seed=seed)
+        theta = torch.tensor(synth.random_torsions(batch, L, seed=seed + 1), device="cuda")
+        E_ref, g_ref = reference(sampler, prot, theta)
+        table = torch.tensor(prot.p, dtype=torch.float64, device="cuda")
+        E = torch.empty(batch, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(theta)
+        amh.amh_grad_noalloc(L, prot.B, table, 0, prot.edges, theta, batch, E, g)
+        torch.cuda.synchronize()
+        # the tolerance the FP32 gradient tests use against the FP64 oracle
+        assert torch.all((E - E_ref).abs() <= 1e-5 * E_ref.abs())
+        for b in range(batch):
+            assert torch.linalg.norm(g[b] - g_ref[b]) <= 1e-3 * torch.linalg.norm(g_ref[b])
+
+
+def test_noalloc_repeated_calls_are_stable_and_neglog_input(mods):
+    torch, amh, sampler = mods
+    L, batch = 40, 4
+    prot = synth.make_protein(L, seed=710)
+    theta = torch.tensor(synth.random_torsions(batch, L, seed=711), device="cuda")
+    E_ref, g_ref = reference(sampler, prot, theta)
+    table = torch.tensor(prot.p, dtype=torch.float64, device="cuda")
+    neglog = -torch.log(table)
+    outs = []
+    for tab, flag in ((table, 0), (neglog, 1)):
+        E = torch.empty(batch, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(theta)
+        amh.amh_grad_noalloc(L, prot.B, tab, flag, prot.edges, theta, batch, E, g)
+        torch.cuda.synchronize()
+        outs.append((E, g))
+        assert torch.all((E - E_ref).abs() <= 1e-5 * E_ref.abs())
+        assert torch.linalg.norm(g - g_ref) <= 1e-3 * torch.linalg.norm(g_ref)
+
+
+def test_noalloc_rejects_tables_beyond_the_static_array(mods):
+    torch, amh, sampler = mods
+    L, B = 400, 37  # 79800 rows x 38 entries > 2^21
+    edges = synth.edges_af1_37()
+    table = torch.zeros(1, dtype=torch.float64, device="cuda")
+    theta = torch.zeros((1, 2 * L), dtype=torch.float32, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.zeros_like(theta)
+    with pytest.raises(amh.AmhError) as ei:
+        amh.amh_grad_noalloc(L, B, table, 0, edges, theta, 1, E, g)
+    assert ei.value.status == amh.AMH_EINVAL
+    assert "static scratch" in str(ei.value)
