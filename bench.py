@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target measurement")
     ap.add_argument("--chains-per-cta", type=int, default=0,
                     help="global-sweep chains per CTA (0 = autotuned)")
     ap.add_argument("--threads", type=int, default=0, help="global-sweep threads per CTA")
@@ -208,6 +209,62 @@ def cpu_baseline(w, seed, budget_s=12.0):
                       "same schedule, FP64, OpenMP over chains" % (
                           cores, s, s // w["cycle"], w["n_local"], w["n_global"], w["L"]),
             "seconds": dt}
+
+
+def time_to_target(stream_cls=None):
+    """Time to a low-energy structure, after the protocol of Sec. 3 / Fig. 4E:
+    the CPU (the FP64 oracle, one chain per core, 10 seeds) runs 1e5
+    proposals of the AMH schedule on the L=150 protein; the target E* is the
+    mean over the 10 runs of the lowest energy seen (at global-sweep ends);
+    the GPU then runs 1024 chains of the same schedule until the lowest
+    energy over its chains reaches E*.  Returns both wall times."""
+    import torch
+    import oracle
+    from paper_2211_03193_gb300 import _amh, synth
+    from paper_2211_03193_gb300.sampler import Sampler
+    w = workload("amh_L150_c1024")
+    L, n = w["L"], w["n"]
+    total = 100000 // n
+    sched = schedule_for(dict(w, total_sweeps=total), seed=2)
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    P = oracle.Problem(L, prot.p, prot.edges)
+    runs = 10
+    S = synth.random_torsions(runs, L, seed=w["start_seed"]).astype(np.float64)
+    best = np.full(runs, np.inf)
+    t0 = time.perf_counter()
+    for s in range(total):
+        mode, T, sigma = sched.params(s)
+        S, _ = P.run_chains(S, mode, w["window"], T, sigma, s * n, n, sched.seed, 0)
+        if mode == _amh.AMH_GLOBAL:
+            best = np.minimum(best, P.energies(S))
+    cpu_s = time.perf_counter() - t0
+    target = float(np.mean(best))
+    chains = w["chains"]
+    stream = torch.cuda.Stream()
+    tors = synth.random_torsions(chains, L, seed=w["start_seed"])
+    samp = Sampler(prot, chains, tors, stream=stream)
+    bE = torch.empty(chains, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reached, s = False, 0
+    with torch.cuda.stream(stream):
+        for s in range(total):
+            mode, T, sigma = sched.params(s)
+            _amh.amh_sweeps(samp.ctx, mode, w["window"], T, sigma, 1, sched.seed, None)
+            if mode == _amh.AMH_GLOBAL:
+                _amh.amh_get_state(samp.ctx, None, None, bE, None)
+                if float(bE.min()) <= target:
+                    reached = True
+                    break
+    gpu_s = time.perf_counter() - t0
+    samp.close()
+    return {"protein": "L=150, 37 bins (amh_L150_c1024 schedule over 1e5 proposals)",
+            "target_energy": target, "cpu_runs": runs, "cpu_seconds": cpu_s,
+            "cpu_proposals_per_run": total * n, "gpu_chains": chains, "gpu_seconds": gpu_s,
+            "gpu_sweeps": s + 1, "reached": reached,
+            "speedup": cpu_s / gpu_s if reached else None,
+            "note": "CPU: FP64 oracle, one chain per core, wall time of the 10 parallel runs"}
 
 
 def run_reference(args):
@@ -360,7 +417,15 @@ def run_ours(args):
                "d2h_bytes_per_step": int(h_out.numel() * 4 + 16 * chains),
                "timing": "host wall clock around set_state + cycle + get_state, synchronised"}
 
+    # the one cross-rank exchange: merge the best states (outside the timed region)
+    th_all, _, bE_all, bt_all = samp.state()
+    if world > 1:
+        from paper_2211_03193_gb300.dist import merge_best
+        best_e, _, best_rank = merge_best(bE_all, bt_all, device="cuda")
+    else:
+        best_e, best_rank = float(np.min(bE_all)), 0
     if rank != 0:
+        samp.close()
         if world > 1:
             dist.destroy_process_group()
         return
@@ -393,9 +458,12 @@ def run_ours(args):
                       "parallelism": "independent chains per GPU (replicas)"},
            "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
            "roofline": roof, "gpu_launches": args.steps * (cyc + 1),
+           "best_energy_all_ranks": best_e, "best_rank": best_rank,
            "clocks": clocks, "e2e": e2e}
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, seed=1)
+    if not args.no_ttt:
+        out["time_to_target"] = time_to_target()
     print(json.dumps(out))
     samp.close()
     if world > 1:

@@ -439,6 +439,7 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   // kernels may use all of the opt-in shared memory
   for (int C = 1; C <= max_C(ctx->precision); C *= 2) CK(ctx, gset<R>(C, ctx->smem_optin));
   CK(ctx, local_set_smem<R>(ctx->smem_optin));
+  CK(ctx, grad_set_smem<R>(ctx->smem_optin));
   // launch shape
   amh_status st;
   if (ctx->opt.chains_per_cta == 0) {

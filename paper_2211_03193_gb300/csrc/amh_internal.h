@@ -98,6 +98,9 @@ cudaError_t local_set_smem(size_t bytes);
 
 // Gradient of V for a batch of torsion vectors of one protein.
 // (prot_host: host copy of the protein's record; only tab_off is read.)
+// grad_set_smem raises the kernel's dynamic shared-memory limit (call once).
+template <class R>
+cudaError_t grad_set_smem(size_t optin);
 template <class R>
 cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R* theta,
                         int batch, double* E_out, R* grad, Tab<R> tab, Geom<R> geom,

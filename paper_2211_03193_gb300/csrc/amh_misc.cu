@@ -206,13 +206,15 @@ inline int grid_for(long long n, int threads) {
 }  // namespace
 
 template <class R>
+cudaError_t grad_set_smem(size_t optin) {
+  return allow_dynamic_smem(grad_kernel<R>, optin);
+}
+
+template <class R>
 cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R* theta, int batch,
                         double* E_out, R* grad, Tab<R> tab, Geom<R> geom, cudaStream_t st) {
   (void)protein;
   const size_t sm = (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1);
-  cudaError_t e = cudaFuncSetAttribute(grad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
   if (batch <= 0) return cudaSuccess;
   grad_kernel<R><<<batch, 256, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab, geom);
   return cudaGetLastError();
@@ -267,6 +269,7 @@ cudaError_t launch_philox_fill(unsigned long long seed, unsigned chain, unsigned
 }
 
 #define AMH_MISC_INST(R)                                                                           \
+  template cudaError_t grad_set_smem<R>(size_t);                                                   \
   template cudaError_t launch_grad<R>(const ProteinDev*, int, int, const R*, int, double*, R*,     \
                                       Tab<R>, Geom<R>, cudaStream_t);                              \
   template cudaError_t launch_prep_table<R>(const double*, long long, int, int, int, R*,           \

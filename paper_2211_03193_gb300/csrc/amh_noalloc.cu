@@ -97,6 +97,17 @@ extern "C" amh_status amh_grad_noalloc(int L, int B, const double* table, int ta
     scratch = g_table_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    static bool smem_set[kMaxDevices] = {false};
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!smem_set[dev]) {
+      cudaDeviceProp prop;
+      e = cudaGetDeviceProperties(&prop, dev);
+      if (e == cudaSuccess) e = grad_set_smem<float>(prop.sharedMemPerBlockOptin);
+      if (e != cudaSuccess) return fail(AMH_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+      smem_set[dev] = true;
+    }
+  }
   e = launch_prep_table<float>(table, rows, B, Bp, table_is_neglog, (float*)scratch, st);
   if (e != cudaSuccess) return fail(AMH_ECUDA, std::string("table kernel: ") + cudaGetErrorString(e));
 

@@ -179,3 +179,22 @@ def run_schedule(sampler: Sampler, sched: Schedule, s0: int = 0, s1: int | None 
         if on_sweep is not None:
             on_sweep(s, mode, T, sigma)
     return total
+
+
+def capture_schedule(sampler: Sampler, sched: Schedule, s0: int, s1: int, stream):
+    """Capture sweeps [s0, s1) of the schedule (one launch per sweep, each with
+    its own T and sigma, plus the noisy restarts) into a CUDA graph on
+    `stream`, which must be the stream the sampler was created with.  Replay
+    runs them again on the device; the chains' proposal counters live in
+    device memory, so each replay continues where the previous one ended.
+    Capturing runs nothing and counts the sweeps once on the host side."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for s in range(s0, s1):
+            mode, T, sigma = sched.params(s)
+            _amh.amh_sweeps(sampler.ctx, mode, sched.window, T, sigma, 1, sched.seed, None)
+            if sched.noisy_every and (s + 1) % sched.noisy_every == 0:
+                _amh.amh_noisy_restart(sampler.ctx, math.radians(sched.noisy_sd_deg),
+                                       sched.seed * 1000003 + s)
+    return g
