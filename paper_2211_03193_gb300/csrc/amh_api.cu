@@ -129,6 +129,7 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   a.acc_out = ctx->acc;
   a.tab = make_tab<R>(ctx);
   a.geom = ideal_geometry<R>();
+  a.geom64 = ideal_geometry<double>();
   a.resync_every = ctx->opt.resync_every;
   a.lattice_K = ctx->opt.lattice_K;
   a.Lmax = ctx->Lmax;
@@ -766,8 +767,9 @@ amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, dou
     return set_err(ctx, AMH_EINVAL, "amh_grad needs device pointers");
   const int L = ctx->L[protein];
   const size_t esz = ctx->precision == 64 ? 8 : 4;
-  const size_t sm = ((esz * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1);
-  if (sm > ctx->smem_optin) return set_err(ctx, AMH_EINVAL, "protein too long for amh_grad");
+  const size_t sm = grad_smem_bytes(esz, L);
+  if (sm > ctx->smem_optin - kStaticSmemMargin)
+    return set_err(ctx, AMH_EINVAL, "protein too long for amh_grad");
   if (ctx->precision == 64) {
     CK(ctx, launch_grad<double>(&ctx->prot_h[protein], protein, L, (const double*)theta, batch,
                                 E_out, (double*)dE_dtheta, make_tab<double>(ctx),

@@ -46,7 +46,10 @@ __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
   return v3<R>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// Correctly rounded 1/sqrt for the builders (NeRF frames, rotation axes):
+// they are off the hot loop, and approximate normalisations there bend the
+// chain systematically.
+__device__ __forceinline__ float rsqrt_(float x) { return __frsqrt_rn(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ void sincos_(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_(double a, double* s, double* c) { sincos(a, s, c); }
@@ -191,6 +194,129 @@ __device__ __forceinline__ Aff<R> identity_map() {
   for (int i = 0; i < 9; ++i) A.m[i] = (i % 4 == 0) ? R(1) : R(0);
   A.t[0] = A.t[1] = A.t[2] = R(0);
   return A;
+}
+
+// ------------------------------------------------------------------ parallel G(s)
+// Every residue is the same rigid body (ideal geometry), so G(s) is a chain
+// of rigid transforms: with residue 0 in the canonical frame of
+// first_residue(), residue i sits at P_i = T_1 o ... o T_i applied to the
+// canonical atoms, where T_i (depending on psi_{i-1} and phi_i only) maps the
+// canonical residue onto residue i as built by NeRF from a canonical residue
+// i-1.  The T_i are computed independently and P_i is a prefix composition,
+// evaluated here as a parallel scan in FP64.
+
+// Orthonormal frame of a residue (columns e1 = CA->C, e2 = CA->N made
+// orthogonal to e1, e3 = e1 x e2) as the rotation part of an affine map.
+__device__ __forceinline__ void residue_frame(V3<double> N, V3<double> CA, V3<double> C,
+                                              double Q[9]) {
+  const V3<double> e1 = unit(C - CA);
+  V3<double> v = N - CA;
+  v = v - e1 * dot(v, e1);
+  const V3<double> e2 = unit(v);
+  const V3<double> e3 = cross(e1, e2);
+  Q[0] = e1.x; Q[1] = e2.x; Q[2] = e3.x;
+  Q[3] = e1.y; Q[4] = e2.y; Q[5] = e3.y;
+  Q[6] = e1.z; Q[7] = e2.z; Q[8] = e3.z;
+}
+
+struct CanonicalResidue {
+  V3<double> N, CA, C, CB;
+  double Q0[9];  // frame of the canonical residue
+};
+
+__device__ __forceinline__ CanonicalResidue canonical_residue(const Geom<double>& g) {
+  CanonicalResidue r;
+  first_residue(g, r.N, r.CA, r.C);
+  r.CB = cbeta(g, r.N, r.CA, r.C);
+  residue_frame(r.N, r.CA, r.C, r.Q0);
+  return r;
+}
+
+// T_i: canonical residue -> residue i in the frame of canonical residue i-1.
+__device__ __forceinline__ Aff<double> residue_step(const Geom<double>& g,
+                                                    const CanonicalResidue& r, double psi,
+                                                    double phi) {
+  V3<double> N = r.N, CA = r.CA, C = r.C;
+  next_residue(g, N, CA, C, psi, phi);
+  double Q1[9];
+  residue_frame(N, CA, C, Q1);
+  Aff<double> T;
+  // M = Q1 Q0^T, t = CA1 - M CA0
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      T.m[3 * i + j] = Q1[3 * i] * r.Q0[3 * j] + Q1[3 * i + 1] * r.Q0[3 * j + 1] +
+                       Q1[3 * i + 2] * r.Q0[3 * j + 2];
+  T.t[0] = CA.x - (T.m[0] * r.CA.x + T.m[1] * r.CA.y + T.m[2] * r.CA.z);
+  T.t[1] = CA.y - (T.m[3] * r.CA.x + T.m[4] * r.CA.y + T.m[5] * r.CA.z);
+  T.t[2] = CA.z - (T.m[6] * r.CA.x + T.m[7] * r.CA.y + T.m[8] * r.CA.z);
+  return T;
+}
+
+__device__ __forceinline__ Aff<double> shfl_up_aff(const Aff<double>& A, int off, int width) {
+  Aff<double> B;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) B.m[i] = __shfl_up_sync(0xffffffffu, A.m[i], off, width);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) B.t[i] = __shfl_up_sync(0xffffffffu, A.t[i], off, width);
+  return B;
+}
+
+// Build G(s) of `nch` chains with all threads of the CTA: chain c uses the
+// tpc = blockDim.x / nslots consecutive threads starting at c * tpc (tpc a
+// power of two).  theta(c, k) reads torsion k of chain c; emit(c, i, N, CA,
+// C, CB) stores residue i.  scratch: nslots * max(tpc/32, 1) * 12 doubles of
+// shared memory.  Must be called by every thread of the CTA.
+template <class TH, class EMIT>
+__device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH theta, EMIT emit,
+                                  double* scratch) {
+  const int tpc = blockDim.x / nslots;
+  const int c = threadIdx.x / tpc, r = threadIdx.x % tpc;
+  const int width = tpc < 32 ? tpc : 32;
+  const int lane = r % width;
+  const int wpc = tpc / width;  // warps per chain
+  const int wi = r / width;     // this thread's warp within its chain
+  const CanonicalResidue cr = canonical_residue(g);
+  const int nb = (L + tpc - 1) / tpc;
+  const int r0 = min(L, r * nb), r1 = min(L, r0 + nb);
+  Aff<double> agg = identity_map<double>();
+  for (int i = max(r0, 1); i < r1; ++i)
+    agg = compose(agg, residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i)));
+  // inclusive scan over the lanes of this chain's warp
+  for (int off = 1; off < width; off <<= 1) {
+    const Aff<double> o = shfl_up_aff(agg, off, width);
+    if (lane >= off) agg = compose(o, agg);
+  }
+  Aff<double> excl = shfl_up_aff(agg, 1, width);
+  if (lane == 0) excl = identity_map<double>();
+  if (wpc > 1) {
+    double* tot = scratch + (size_t)(c * wpc + wi) * 12;
+    if (lane == width - 1) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) tot[q] = agg.m[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) tot[9 + q] = agg.t[q];
+    }
+    __syncthreads();
+    Aff<double> pre = identity_map<double>();
+    for (int w = 0; w < wi; ++w) {
+      const double* tw = scratch + (size_t)(c * wpc + w) * 12;
+      Aff<double> A;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) A.m[q] = tw[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) A.t[q] = tw[9 + q];
+      pre = compose(pre, A);
+    }
+    excl = compose(pre, excl);
+    __syncthreads();
+  }
+  Aff<double> P = excl;
+  for (int i = r0; i < r1; ++i) {
+    if (i >= 1) P = compose(P, residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i)));
+    emit(c, i, apply(P, cr.N), apply(P, cr.CA), apply(P, cr.C), apply(P, cr.CB));
+  }
 }
 
 // ------------------------------------------------------------------ table

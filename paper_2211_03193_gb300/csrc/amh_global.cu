@@ -34,8 +34,8 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cbx, cby, cbz, maps, part, ecur, thn, lnu, acc, commit, flag, bars, ring,
-      total;
+  size_t theta, bb, cbx, cby, cbz, maps, part, ecur, thn, lnu, acc, commit, flag, scan, bars,
+      ring, total;
   // D ring slots per warp of 32/C rows of RB bytes (D = 0: no staging)
   __host__ __device__ Layout(int Lmax, int nmax, int W, int D = 0, int RB = 0) {
     size_t o = 0;
@@ -52,6 +52,7 @@ struct Layout {
     acc = o;   o = align16(o + sizeof(long long) * C);
     commit = o; o = align16(o + sizeof(int) * C);
     flag = o;  o = align16(o + sizeof(int) * C);
+    scan = o;  o = align16(o + sizeof(double) * 12 * (size_t)W);
     bars = o;  o = align16(o + sizeof(unsigned long long) * (size_t)W * D);
     o = (o + 127) & ~size_t(127);
     ring = o;  o = align16(o + (size_t)W * D * (32 / C) * RB);
@@ -74,6 +75,7 @@ struct Shm {
   long long* acc;
   int* commit;
   int* flag;
+  double* scan;              // [W][12] warp totals of the chain-building scan
   unsigned long long* bars;  // [W][D] mbarriers of the staging rings
   unsigned char* ring;       // [W][D][32/C][RB] staged table rows
   __device__ Shm(unsigned char* base, const Layout<R, C>& l) {
@@ -90,6 +92,7 @@ struct Shm {
     acc = (long long*)(base + l.acc);
     commit = (int*)(base + l.commit);
     flag = (int*)(base + l.flag);
+    scan = (double*)(base + l.scan);
     bars = (unsigned long long*)(base + l.bars);
     ring = base + l.ring;
   }
@@ -108,22 +111,28 @@ struct Shm {
   }
 };
 
-// G(s) of chain slot c (one thread, serial along the chain).
+template <class R>
+__device__ __forceinline__ V3<R> to_r(V3<double> v) {
+  return v3<R>((R)v.x, (R)v.y, (R)v.z);
+}
+
+// G(s) of all C chain slots, built in FP64 by all threads (a parallel scan
+// of residue transforms) and stored in R: rounding the torsions' sines and
+// cosines in single precision would random-walk the frame along the chain
+// (~1e-4 A at L=300).
 template <class R, int C>
-__device__ void build_chain(Shm<R, C>& s, const Geom<R>& g, int L, int c) {
-  V3<R> N, CA, Cc;
-  first_residue(g, N, CA, Cc);
-  for (int i = 0;; ++i) {
-    s.set_atom(i, 0, c, N);
-    s.set_atom(i, 1, c, CA);
-    s.set_atom(i, 2, c, Cc);
-    V3<R> cb = cbeta(g, N, CA, Cc);
-    s.cbx[i * C + c] = cb.x;
-    s.cby[i * C + c] = cb.y;
-    s.cbz[i * C + c] = cb.z;
-    if (i + 1 >= L) break;
-    next_residue(g, N, CA, Cc, s.theta[(2 * i + 1) * C + c], s.theta[(2 * i + 2) * C + c]);
-  }
+__device__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
+  build_chains_scan(
+      g, L, C, [&](int c, int k) { return (double)s.theta[k * C + c]; },
+      [&](int c, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
+        s.set_atom(i, 0, c, to_r<R>(N));
+        s.set_atom(i, 1, c, to_r<R>(CA));
+        s.set_atom(i, 2, c, to_r<R>(Cc));
+        s.cbx[i * C + c] = (R)CB.x;
+        s.cby[i * C + c] = (R)CB.y;
+        s.cbz[i * C + c] = (R)CB.z;
+      },
+      s.scan);
 }
 
 // Reduce three per-lane partial sums over the slices of each chain and
@@ -180,7 +189,7 @@ __device__ void full_energy(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, i
 template <class R, int C>
 __device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P) {
   __syncthreads();
-  if (threadIdx.x < C) build_chain(s, a.geom, P.L, threadIdx.x);
+  build_chains(s, a.geom64, P.L);
   __syncthreads();
   full_energy(s, a.tab, P.tab_off, P.L);
 }

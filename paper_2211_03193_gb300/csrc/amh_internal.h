@@ -55,6 +55,7 @@ struct SweepArgs {
   long long* acc_out;  // per chain accepted count of this call (may be null)
   Tab<R> tab;
   Geom<R> geom;
+  Geom<double> geom64;  // the resync rebuilds G(s) in FP64 (stored in R)
   double T;
   R sigma;
   unsigned long long seed;
@@ -99,6 +100,7 @@ cudaError_t local_set_smem(size_t bytes);
 // Gradient of V for a batch of torsion vectors of one protein.
 // (prot_host: host copy of the protein's record; only tab_off is read.)
 // grad_set_smem raises the kernel's dynamic shared-memory limit (call once).
+size_t grad_smem_bytes(size_t rsize, int L);
 template <class R>
 cudaError_t grad_set_smem(size_t optin);
 template <class R>

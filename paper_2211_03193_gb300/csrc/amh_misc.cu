@@ -4,6 +4,13 @@
 
 namespace amh {
 
+// Shared memory of one gradient CTA (256 threads): coordinates and forces in
+// R, suffix sums in FP64, and the chain-building scan's warp totals.
+size_t grad_smem_bytes(size_t rsize, int L) {
+  return ((rsize * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1) +
+         sizeof(double) * 12 * 8;
+}
+
 namespace {
 
 // ---------------------------------------------------------------- gradient
@@ -15,31 +22,29 @@ namespace {
 template <class R>
 __global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, const R* __restrict__ theta,
                                                    double* __restrict__ E_out, R* __restrict__ grad,
-                                                   Tab<R> tb, Geom<R> geom) {
+                                                   Tab<R> tb, Geom<double> geom) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = 2 * L;
   R* X = (R*)smem;          // [4][L][3]: N, CA, C, CB
   R* gb = X + 12 * L;       // [L][3] dV/dx_b
   double* GM = (double*)(smem + (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15));  // [L+1][6]
+  double* scan = GM + (size_t)6 * (L + 1);  // [warps][12] for the chain-building scan
   __shared__ double wpart[32];
   const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const R* th = theta + (size_t)v * n;
-  if (tid == 0) {
-    V3<R> N, CA, Cc;
-    first_residue(geom, N, CA, Cc);
-    for (int i = 0;; ++i) {
-      V3<R> cb = cbeta(geom, N, CA, Cc);
-      const V3<R> at[4] = {N, CA, Cc, cb};
+  // G(s) built in FP64 by all threads, stored in R (as the sweeps' resync)
+  build_chains_scan(
+      geom, L, 1, [&](int, int k) { return (double)th[k]; },
+      [&](int, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
+        const V3<double> at[4] = {N, CA, Cc, CB};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        X[(q * L + i) * 3 + 0] = at[q].x;
-        X[(q * L + i) * 3 + 1] = at[q].y;
-        X[(q * L + i) * 3 + 2] = at[q].z;
-      }
-      if (i + 1 >= L) break;
-      next_residue(geom, N, CA, Cc, th[2 * i + 1], th[2 * i + 2]);
-    }
-  }
+        for (int q = 0; q < 4; ++q) {
+          X[(q * L + i) * 3 + 0] = (R)at[q].x;
+          X[(q * L + i) * 3 + 1] = (R)at[q].y;
+          X[(q * L + i) * 3 + 2] = (R)at[q].z;
+        }
+      },
+      scan);
   __syncthreads();
   const R* CB = X + 9 * L;
   double esum = 0.0;
@@ -214,9 +219,11 @@ template <class R>
 cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R* theta, int batch,
                         double* E_out, R* grad, Tab<R> tab, Geom<R> geom, cudaStream_t st) {
   (void)protein;
-  const size_t sm = (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1);
+  const size_t sm = grad_smem_bytes(sizeof(R), L);
   if (batch <= 0) return cudaSuccess;
-  grad_kernel<R><<<batch, 256, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab, geom);
+  (void)geom;
+  grad_kernel<R><<<batch, 256, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab,
+                                         ideal_geometry<double>());
   return cudaGetLastError();
 }
 

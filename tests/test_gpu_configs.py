@@ -1,0 +1,152 @@
+"""Parity at the workload configurations: the FP64 single chain (exact
+trajectory), the bench's L=300 / 1024-chain launch (sampled chains), 64
+proteins of uneven length in one context, and L=500 with 64 bins (FP32
+against the FP64 GPU form).  Expected values come from the oracle only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2211_03193_gb300 import synth
+from test_gpu_parity import replay_and_compare
+
+pytestmark = pytest.mark.gpu
+DEG = math.pi / 180
+
+
+@pytest.fixture(scope="module")
+def amh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_03193_gb300 import build, _amh, sampler
+    build.build()
+    _amh.load()
+    return sampler
+
+
+def test_fp64_single_chain_amh_trajectory_equals_oracle(amh, orc):
+    """L=64, one chain, FP64, sigma 15 deg, d=8, T=1, 10 local : 1 global:
+    156 whole sweeps (19 968 proposals; a local sweep cannot stop part-way).
+    No teacher forcing: every decision must match the oracle's."""
+    L = 64
+    n = 2 * L
+    prot = synth.make_protein(L, seed=1000)
+    tors = synth.random_torsions(1, L, seed=8)
+    sweeps = 156
+    sigma, T, d = 15 * DEG, 1.0, 8
+    P = orc.Problem(L, prot.p, prot.edges)
+    s_orc = tors[0].astype(np.float64)
+    with amh.Sampler(prot, 1, tors, precision=64, trace_chains=1,
+                     trace_capacity=sweeps * n) as s:
+        trs = []
+        for q in range(sweeps):
+            mode = 0 if q % 11 < 10 else 1
+            s.sweeps(mode, d, T, sigma, 1, 3)
+            s_orc, _, tr = P.run(s_orc, orc.LOCAL if mode == 0 else orc.GLOBAL, d, T, sigma,
+                                 q * n, n, 3, 0, trace=True)
+            trs.append(tr)
+        gt = s.trace(0)
+        ot = np.concatenate(trs)
+        assert gt.shape[0] == sweeps * n
+        diff = np.flatnonzero(gt["accept"] != ot["accept"])
+        if diff.size:
+            j = diff[0]
+            assert abs(ot["lnu"][j] + ot["dV"][j] / T) < 1e-5, j
+        else:
+            assert np.allclose(s.torsions()[0], s_orc, atol=1e-6)
+            assert np.allclose(gt["dE"], ot["dV"], atol=1e-8, rtol=1e-9)
+        # a local sweep leaves the stored energy at the last global sweep's:
+        # recompute it
+        E = s.energy()
+        assert abs(E[0] - P.energy(s_orc)) <= 1e-10 * abs(E[0])
+
+
+def test_bench_workload_sampled_parity(amh, orc):
+    """L=300, 1024 chains, the autotuned launch shape the bench times, one AMH
+    cycle of the bench schedule; chains 0-2 traced and replayed by the oracle,
+    eight chains' end energies recomputed by the oracle."""
+    import bench
+    w = bench.workload("amh_L300_c1024")
+    L, n, chains = w["L"], w["n"], w["chains"]
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    tors = synth.random_torsions(chains, L, seed=w["start_seed"])
+    sched = bench.schedule_for(w, seed=1)
+    P = orc.Problem(L, prot.p, prot.edges)
+    with amh.Sampler(prot, chains, tors, trace_chains=3, trace_capacity=w["cycle"] * n) as s:
+        for q in range(w["cycle"]):
+            mode, T, sigma = sched.params(q)
+            s.sweeps(mode, w["window"], T, sigma, 1, sched.seed)
+        th, E, bE, _ = s.state()
+        th = th.reshape(chains, n)
+        for c in range(3):
+            tr = s.trace(c)
+            st = tors[c]
+            for q in range(w["cycle"]):
+                mode, T, sigma = sched.params(q)
+                seg = tr[q * n:(q + 1) * n]
+                d = replay_and_compare(orc, prot, st, seg, orc.LOCAL if mode == 0 else orc.GLOBAL,
+                                       w["window"], T, sigma, q * n, sched.seed, c, False)
+                st = d["s_end"]
+            assert np.allclose(np.angle(np.exp(1j * (th[c] - st))), 0, atol=1e-4)
+    for c in (0, 1, 255, 256, 511, 640, 1022, 1023):
+        e = P.energy(th[c].astype(np.float64))
+        assert abs(E[c] - e) <= 1e-5 * abs(e), c
+        assert bE[c] <= E[c] + 1e-9
+
+
+def test_uneven_proteins_one_context(amh, orc):
+    """64 proteins, L uniform in [50, 400], 256 chains each (16 384 chains):
+    one local and one global sweep per chain through the persistent queue."""
+    Ls = synth.uneven_lengths(64, 50, 400, seed=3)
+    prots = [synth.make_protein(L, seed=2000 + i) for i, L in enumerate(Ls)]
+    chains = [256] * 64
+    tors = np.concatenate([synth.random_torsions(256, L, seed=3000 + i).ravel()
+                           for i, L in enumerate(Ls)])
+    T, sigma = 1.0, 10 * DEG
+    with amh.Sampler(prots, chains, tors, trace_chains=2, trace_capacity=4 * Ls[0]) as s:
+        s.sweeps(0, 8, T, sigma, 1, 9)
+        s.sweeps(1, 0, T, sigma, 1, 9)
+        th, E, bE, _ = s.state()
+        for c in range(2):
+            tr = s.trace(c)
+            n0 = 2 * Ls[0]
+            d = replay_and_compare(orc, prots[0], tors[c * n0:(c + 1) * n0], tr[:n0], orc.LOCAL,
+                                   8, T, sigma, 0, 9, c, False)
+            replay_and_compare(orc, prots[0], d["s_end"], tr[n0:], orc.GLOBAL, 0, T, sigma, n0,
+                               9, c, False)
+        for p in (0, 7, 21, 40, 63):
+            off = s.offsets[p]
+            n = prots[p].n
+            P = orc.Problem(prots[p].L, prots[p].p, prots[p].edges)
+            for c in (0, 255):
+                chain = 256 * p + c
+                assert s.counter(chain) == 2 * n
+                e = P.energy(th[off + c * n: off + (c + 1) * n].astype(np.float64))
+                assert abs(E[chain] - e) <= 1e-5 * abs(e)
+
+
+def test_l500_64bins_fp32_against_fp64(amh, orc):
+    """L=500, 4096 chains, 64 bins of 0.3125 A (sigma_d 1.5 A): after two
+    local and one global FP32 sweep, the FP32 energies agree with the FP64
+    GPU form's energies of the same states to 1e-4 relative, and both with
+    the oracle on sampled chains."""
+    L, chains = 500, 4096
+    prot = synth.make_protein(L, edges=synth.edges_uniform_64(), sigma_d=1.5, seed=1000)
+    tors = synth.random_torsions(chains, L, seed=12)
+    with amh.Sampler(prot, chains, tors) as s32:
+        s32.sweeps(0, 8, 1.0, 8 * DEG, 2, 5)
+        s32.sweeps(1, 0, 1.0, 8 * DEG, 1, 5)
+        th, E32, _, _ = s32.state()
+    with amh.Sampler(prot, chains, th, precision=64) as s64:
+        E64 = s64.energy()
+    rel = np.abs(E32 - E64) / np.abs(E64)
+    i = int(np.nanargmax(rel))
+    assert np.all(rel <= 1e-4), (i, E32[i], E64[i], rel[i], int(np.isnan(E32).sum()))
+    P = orc.Problem(L, prot.p, prot.edges)
+    th = th.reshape(chains, 2 * L)
+    for c in (0, 2047, 4095):
+        e = P.energy(th[c].astype(np.float64))
+        assert abs(E64[c] - e) <= 1e-11 * abs(e)
+        assert abs(E32[c] - e) <= 1e-5 * abs(e)
