@@ -218,12 +218,6 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
   constexpr int S = 32 / C;
   const int c = lane % C, sl = lane / C;
   const int gs = warp * S + sl, G = W * S;
-  Aff<R> A1, A2, A21;
-  load_aff<R, C>(s.maps + 36 * c, A1);
-  if (FUSED) {
-    load_aff<R, C>(s.maps + 36 * c + 12, A2);
-    load_aff<R, C>(s.maps + 36 * c + 24, A21);
-  }
   const int nF = f1 - f0;
   const int nch = (nF + kFC - 1) / kFC;
   const int items = (m1 - m0) * nch;
@@ -232,11 +226,17 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     const int mi = it / nch, ch = it - mi * nch;
     const int m = m0 + mi;
     const V3<R> xm = s.cb(m, c);
-    const V3<R> y1 = apply(A1, xm);
+    // the maps are read per item (only the moved positions stay live in the
+    // pair loop, leaving registers for more loads in flight)
+    Aff<R> A;
+    load_aff<R, C>(s.maps + 36 * c, A);
+    const V3<R> y1 = apply(A, xm);
     V3<R> y2, y21;
     if (FUSED) {
-      y2 = apply(A2, xm);
-      y21 = apply(A21, xm);
+      load_aff<R, C>(s.maps + 36 * c + 12, A);
+      y2 = apply(A, xm);
+      load_aff<R, C>(s.maps + 36 * c + 24, A);
+      y21 = apply(A, xm);
     }
     const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
     // rows of the pairs (f, m): contiguous in f when m < f; when f < m,
@@ -246,7 +246,7 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
         tb.E + tab_off + (long long)(mfirst ? row_of(L, m, fb) : row_of(L, fb, m)) * tb.Bp;
     int step = mfirst ? 1 : L - fb - 2;
     const int dstep = mfirst ? 0 : -1;
-#pragma unroll 2
+#pragma unroll 4
     for (int f = fb; f < fe; ++f) {
       const V3<R> xf = s.cb(f, c);
       const R e0 = pair_term(row, dist_(xf, xm), tb);
