@@ -186,6 +186,31 @@ amh_status amh_set_state(amh_ctx* ctx, const float* torsions);
  * recomputed (the noisy-restart baseline of Sec. 3).                       */
 amh_status amh_noisy_restart(amh_ctx* ctx, double sd_rad, unsigned long long seed);
 
+/*
+ * amh_set_ladder -- parallel tempering (one of the coordinated multi-chain
+ * schemes Sec. 2.4 names for chains run side by side): the chains of every
+ * protein form ladders of K consecutive chains, and slot j of a ladder
+ * runs its sweeps at T * ladder[j] (T the sweep call's temperature, so an
+ * anneal scales the whole ladder).  Every protein's chain count must be a
+ * multiple of K.  K = 0 removes the ladder.  ladder: host, K positive
+ * factors, ascending for the usual ordering.
+ */
+amh_status amh_set_ladder(amh_ctx* ctx, int K, const double* ladder);
+
+/*
+ * amh_exchange -- one round of replica exchange: for every ladder slot j
+ * with j = parity (mod 2) and j+1 < K, the states of slots j and j+1 are
+ * swapped iff ln u < (1/T_j - 1/T_{j+1}) (E_j - E_{j+1}) with T_j = T *
+ * ladder[j] (the Metropolis rule for exchanging two replicas), u from
+ * Philox4x32-10 at counter (chain of slot j, round low, round high, 3)
+ * where round counts this context's exchange calls.  Uses the stored
+ * energies: call it after a global sweep or amh_energy.  swapped_out: NULL
+ * or [total chains] long long (host or device), 1 at the lower slot of each
+ * swapped pair.
+ */
+amh_status amh_exchange(amh_ctx* ctx, double T, int parity, unsigned long long seed,
+                        long long* swapped_out);
+
 /* amh_get_trace -- copy the trace of chain `chain` (< trace_chains):
  * records [0, min(count, trace_capacity)) in visit order into `out` (host),
  * *count set to the records written so far.                              */

@@ -90,6 +90,9 @@ def lib():
     L.orc_noisy_restart.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_uint64,
                                     ctypes.c_uint32]
     L.orc_grad.argtypes = [ctypes.c_void_p, dp, dp, dp]
+    L.orc_exchange.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, dp,
+                               dp, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
 
@@ -222,6 +225,21 @@ class Problem:
         V = ctypes.c_double()
         lib().orc_grad(self._h, _dp(s), ctypes.byref(V), _dp(g))
         return V.value, g
+
+
+def exchange(E, S, K: int, ladder, T_scale: float, parity: int, seed: int, round_: int,
+             chain0: int = 0):
+    """Replica exchange between neighbouring ladder slots; returns new (E, S,
+    accepted) -- see orc_exchange."""
+    E = _f64(E).copy()
+    S = _f64(S).copy()
+    nch = E.shape[0]
+    n = S.size // nch
+    ladder = _f64(ladder)
+    acc = np.zeros(nch, dtype=np.int32)
+    lib().orc_exchange(nch, n, K, _dp(ladder), T_scale, parity, seed, round_, chain0, _dp(E),
+                       _dp(S), acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return E, S.reshape(nch, n), acc
 
 
 def noisy_restart(s, sd: float, seed: int, chain: int) -> np.ndarray:

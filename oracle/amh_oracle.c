@@ -463,3 +463,41 @@ void orc_grad(const orc_problem* P, const double* s, double* V_out, double* g) {
   }
   free(N); free(CA); free(C); free(CB);
 }
+
+/* ------------------------------------------------------------------ */
+/* Replica exchange between neighbouring temperatures (parallel tempering,
+ * one of the coordinated multi-chain schemes Sec. 2.4 lists for the
+ * chains a GPU runs side by side; Hansmann 1997).  Chains are grouped in
+ * ladders of K consecutive chains; slot j of a ladder runs at temperature
+ * T_scale * ladder[j].  For every pair of slots (j, j+1) with j = parity
+ * (mod 2), the states are swapped iff ln u < (1/T_j - 1/T_{j+1})(E_j - E_{j+1}),
+ * u at Philox counter (chain of slot j, round low, round high, 3): the
+ * Metropolis rule for exchanging two replicas of exp(-E/T) (u from Philox
+ * stream 3).  E and the torsions s[nchains][n] are swapped together;
+ * accepted[chain of slot j] is set to 1 for an exchange.                 */
+void orc_exchange(int nchains, int n, int K, const double* ladder, double T_scale, int parity,
+                  uint64_t seed, uint64_t round, uint32_t chain0, double* E, double* s,
+                  int* accepted) {
+  for (int c = 0; c < nchains; ++c) accepted[c] = 0;
+  for (int base = 0; base + K <= nchains; base += K) {
+    for (int j = parity; j + 1 < K; j += 2) {
+      int a = base + j, b = base + j + 1;
+      double Ta = T_scale * ladder[j], Tb = T_scale * ladder[j + 1];
+      uint32_t w[4];
+      uint32_t ctr[4] = {chain0 + (uint32_t)a, (uint32_t)round, (uint32_t)(round >> 32), 3u};
+      uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      orc_philox4x32_10(ctr, key, w);
+      double lnu = log(uniform23(w[0]));
+      double delta = (1.0 / Ta - 1.0 / Tb) * (E[a] - E[b]);
+      if (lnu < delta) {
+        double t = E[a]; E[a] = E[b]; E[b] = t;
+        for (int k = 0; k < n; ++k) {
+          double q = s[(size_t)a * n + k];
+          s[(size_t)a * n + k] = s[(size_t)b * n + k];
+          s[(size_t)b * n + k] = q;
+        }
+        accepted[a] = 1;
+      }
+    }
+  }
+}

@@ -77,11 +77,14 @@ def load() -> ctypes.CDLL:
     L.amh_launch_config.argtypes = [vp, ip, ip, ip]
     L.amh_destroy.argtypes = [vp]
     L.amh_destroy.restype = None
+    L.amh_set_ladder.argtypes = [vp, ctypes.c_int, vp]
+    L.amh_exchange.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_ulonglong, vp]
     L.amh_grad_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp,
                                    ctypes.c_int, vp, vp, vp]
     for name in ("amh_init", "amh_energy", "amh_sweep", "amh_sweeps", "amh_grad", "amh_get_state",
                  "amh_set_state", "amh_noisy_restart", "amh_get_trace", "amh_counter",
-                 "amh_philox", "amh_launch_config", "amh_grad_noalloc"):
+                 "amh_philox", "amh_launch_config", "amh_grad_noalloc", "amh_set_ladder",
+                 "amh_exchange"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -179,6 +182,20 @@ def amh_get_trace(ctx, chain, capacity):
     return out[:cnt.value]
 
 
+def amh_set_ladder(ctx, ladder):
+    """Temperature ladder factors (host array of K >= 2), or None to clear."""
+    if ladder is None:
+        _check(load().amh_set_ladder(ctx, 0, None), ctx)
+        return
+    lad = np.ascontiguousarray(ladder, dtype=np.float64)
+    _check(load().amh_set_ladder(ctx, int(lad.shape[0]), lad.ctypes.data), ctx)
+
+
+def amh_exchange(ctx, T, parity, seed, swapped_out=None):
+    _check(load().amh_exchange(ctx, float(T), int(parity), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                               _ptr(swapped_out)), ctx)
+
+
 def amh_counter(ctx, chain) -> int:
     t = ctypes.c_longlong()
     _check(load().amh_counter(ctx, int(chain), ctypes.byref(t)), ctx)
@@ -225,4 +242,4 @@ def amh_grad_noalloc(L, B, table, table_is_neglog, edges, theta, batch, E_out, d
 EXPORTED = ["amh_options_default", "amh_init", "amh_energy", "amh_sweep", "amh_sweeps",
             "amh_grad", "amh_get_state", "amh_set_state", "amh_noisy_restart", "amh_get_trace",
             "amh_counter", "amh_philox", "amh_last_error", "amh_launch_config", "amh_destroy",
-            "amh_grad_noalloc"]
+            "amh_grad_noalloc", "amh_set_ladder", "amh_exchange"]

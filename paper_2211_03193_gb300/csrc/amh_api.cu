@@ -50,6 +50,9 @@ struct amh_ctx {
   // launch configuration
   int C = 8, threads = 256, grid_global = 1;
   int stage_depth = 0;  // > 0: global sweeps stage table rows through shared memory
+  double* ladder = nullptr;  // parallel tempering: per-slot temperature factors
+  int ladder_K = 0;
+  unsigned long long xround = 0;  // exchange rounds so far (Philox counter)
   int sm_count = 1;
   size_t smem_optin = 0;
   std::string msg;
@@ -140,6 +143,8 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   a.trace_count = ctx->trace_count;
   a.err = ctx->err;
   a.stage_depth = ctx->stage_depth;
+  a.ladder = ctx->ladder_K ? ctx->ladder : nullptr;
+  a.ladder_K = ctx->ladder_K;
   return a;
 }
 
@@ -519,7 +524,7 @@ void free_ctx(amh_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
                   ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
-                  ctx->queue, ctx->err, ctx->trace, ctx->trace_count};
+                  ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 6; ++q)
@@ -866,6 +871,56 @@ amh_status amh_get_trace(amh_ctx* ctx, int chain, amh_trace_rec* out, long long*
     CK(ctx, cudaMemcpyAsync(out, ctx->trace + (size_t)chain * ctx->opt.trace_capacity,
                             sizeof(TraceRec) * (size_t)cnt, cudaMemcpyDefault, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return AMH_OK;
+}
+
+amh_status amh_set_ladder(amh_ctx* ctx, int K, const double* ladder) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (K == 0) {
+    ctx->ladder_K = 0;
+    return AMH_OK;
+  }
+  if (K < 2 || !ladder) return set_err(ctx, AMH_EINVAL, "a ladder needs K >= 2 factors");
+  for (int p = 0; p < ctx->nprot; ++p)
+    if (ctx->nch[p] % K != 0)
+      return set_err(ctx, AMH_EINVAL, "every protein's chain count must be a multiple of K");
+  for (int j = 0; j < K; ++j)
+    if (!(ladder[j] > 0) || !std::isfinite(ladder[j]))
+      return set_err(ctx, AMH_EINVAL, "ladder factors must be positive");
+  if (ctx->ladder) {
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->ladder);
+    ctx->ladder = nullptr;
+  }
+  CK(ctx, cudaMalloc(&ctx->ladder, sizeof(double) * K));
+  CK(ctx, cudaMemcpy(ctx->ladder, ladder, sizeof(double) * K, cudaMemcpyHostToDevice));
+  ctx->ladder_K = K;
+  return AMH_OK;
+}
+
+amh_status amh_exchange(amh_ctx* ctx, double T, int parity, unsigned long long seed,
+                        long long* swapped_out) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!ctx->ladder_K) return set_err(ctx, AMH_EINVAL, "no temperature ladder set");
+  if (!(T > 0) || !std::isfinite(T) || (parity != 0 && parity != 1))
+    return set_err(ctx, AMH_EINVAL, "T must be positive and parity 0 or 1");
+  if (ctx->precision == 64) {
+    CK(ctx, launch_exchange<double>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains,
+                                    ctx->ladder_K, ctx->ladder, T, parity, seed, ctx->xround,
+                                    (double*)ctx->theta, ctx->E_cur, ctx->acc, ctx->stream));
+  } else {
+    CK(ctx, launch_exchange<float>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains,
+                                   ctx->ladder_K, ctx->ladder, T, parity, seed, ctx->xround,
+                                   (float*)ctx->theta, ctx->E_cur, ctx->acc, ctx->stream));
+  }
+  ++ctx->xround;
+  if (swapped_out) {
+    CK(ctx, cudaMemcpyAsync(swapped_out, ctx->acc, sizeof(long long) * ctx->total_chains,
+                            cudaMemcpyDefault, ctx->stream));
+    if (!is_device_ptr(swapped_out)) CK(ctx, cudaStreamSynchronize(ctx->stream));
   }
   return AMH_OK;
 }

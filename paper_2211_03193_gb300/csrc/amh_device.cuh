@@ -267,10 +267,12 @@ __device__ __forceinline__ Aff<double> shfl_up_aff(const Aff<double>& A, int off
 // tpc = blockDim.x / nslots consecutive threads starting at c * tpc (tpc a
 // power of two).  theta(c, k) reads torsion k of chain c; emit(c, i, N, CA,
 // C, CB) stores residue i.  scratch: nslots * max(tpc/32, 1) * 12 doubles of
-// shared memory.  Must be called by every thread of the CTA.
+// shared memory.  cache (optional, nslots * L * 12 doubles of shared memory)
+// keeps each T_i so the second pass does not recompute it.  Must be called
+// by every thread of the CTA.
 template <class TH, class EMIT>
 __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH theta, EMIT emit,
-                                  double* scratch) {
+                                  double* scratch, double* cache = nullptr) {
   const int tpc = blockDim.x / nslots;
   const int c = threadIdx.x / tpc, r = threadIdx.x % tpc;
   const int width = tpc < 32 ? tpc : 32;
@@ -281,8 +283,17 @@ __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH t
   const int nb = (L + tpc - 1) / tpc;
   const int r0 = min(L, r * nb), r1 = min(L, r0 + nb);
   Aff<double> agg = identity_map<double>();
-  for (int i = max(r0, 1); i < r1; ++i)
-    agg = compose(agg, residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i)));
+  for (int i = max(r0, 1); i < r1; ++i) {
+    const Aff<double> T = residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i));
+    if (cache) {
+      double* q = cache + ((size_t)c * L + i) * 12;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) q[k] = T.m[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q[9 + k] = T.t[k];
+    }
+    agg = compose(agg, T);
+  }
   // inclusive scan over the lanes of this chain's warp
   for (int off = 1; off < width; off <<= 1) {
     const Aff<double> o = shfl_up_aff(agg, off, width);
@@ -314,7 +325,19 @@ __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH t
   }
   Aff<double> P = excl;
   for (int i = r0; i < r1; ++i) {
-    if (i >= 1) P = compose(P, residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i)));
+    if (i >= 1) {
+      Aff<double> T;
+      if (cache) {
+        const double* q = cache + ((size_t)c * L + i) * 12;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) T.m[k] = q[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) T.t[k] = q[9 + k];
+      } else {
+        T = residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i));
+      }
+      P = compose(P, T);
+    }
     emit(c, i, apply(P, cr.N), apply(P, cr.CA), apply(P, cr.C), apply(P, cr.CB));
   }
 }

@@ -429,6 +429,13 @@ __device__ void commit_moves(Shm<R, C>& s, int m0, int m1) {
   }
 }
 
+// Temperature of chain slot c: T, times its ladder factor under parallel
+// tempering.
+template <class R>
+__device__ __forceinline__ double chain_T(const SweepArgs<R>& a, const ProteinDev& P, int chain) {
+  return a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
+}
+
 template <class R>
 __device__ __forceinline__ void put_trace(const SweepArgs<R>& a, bool real, int chain, long long v,
                                           int k, int acc, R thn, R lnu, double dE) {
@@ -562,7 +569,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       if (threadIdx.x < C) {
         const int c = threadIdx.x;
         const int chain = G.chain0 + c;
-        const int acc = (double)s.lnu[c] < -0.0 / a.T;
+        const int acc = (double)s.lnu[c] < -0.0 / chain_T(a, P, chain);
         if (acc) s.theta[k * C + c] = s.thn[c];
         s.acc[c] += acc;
         put_trace(a, c < G.nchains, chain, t, k, acc, s.thn[c], s.lnu[c], 0.0);
@@ -598,7 +605,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         d2 += pp[1];
         d21 += pp[2];
       }
-      const int acc1 = (double)s.lnu[c] < -d1 / a.T;
+      const double Tc = chain_T(a, P, chain);
+      const int acc1 = (double)s.lnu[c] < -d1 / Tc;
       int code = acc1;
       double dE = acc1 ? d1 : 0.0;
       if (acc1) s.theta[k * C + c] = s.thn[c];
@@ -606,7 +614,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       int acc2 = 0;
       if (fused) {
         const double e2 = acc1 ? d21 : d2;
-        acc2 = (double)s.lnu[C + c] < -e2 / a.T;
+        acc2 = (double)s.lnu[C + c] < -e2 / Tc;
         if (acc2) {
           code = acc1 ? 3 : 2;
           dE += e2;

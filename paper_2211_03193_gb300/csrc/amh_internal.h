@@ -65,6 +65,8 @@ struct SweepArgs {
   int lattice_K;
   int window;           // local sweeps: d
   int stage_depth;      // global sweeps, staged variant: ring slots per warp
+  const double* ladder; // per-slot temperature factors (parallel tempering) or null
+  int ladder_K;         // ladder size: chain c of protein p runs at T * ladder[(c - chain0) % K]
   int Lmax, nmax;       // smem sizing
   TraceRec* trace;
   int trace_chains;
@@ -130,6 +132,13 @@ template <class R>
 cudaError_t launch_convert_in(const float* src, R* dst, long long count, cudaStream_t st);
 template <class R>
 cudaError_t launch_convert_out(const R* src, float* dst, long long count, cudaStream_t st);
+
+// Replica exchange between neighbouring ladder slots of parity `parity`.
+template <class R>
+cudaError_t launch_exchange(const ProteinDev* prot, const int* chain_prot, int nchains, int K,
+                            const double* ladder, double T_scale, int parity,
+                            unsigned long long seed, unsigned long long round, R* theta,
+                            double* E, long long* accepted, cudaStream_t st);
 
 cudaError_t launch_philox_fill(unsigned long long seed, unsigned chain, unsigned long long t0,
                                unsigned stream, long long count, uint4* words, float* z, float* u,

@@ -7,9 +7,12 @@ namespace amh {
 // Shared memory of one gradient CTA (256 threads): coordinates and forces in
 // R, suffix sums in FP64, and the chain-building scan's warp totals.
 size_t grad_smem_bytes(size_t rsize, int L) {
-  return ((rsize * 15 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1) +
+  return ((rsize * 18 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1) +
          sizeof(double) * 12 * 8;
 }
+
+// The residue-transform cache (12 doubles per residue) is used when it fits.
+static size_t grad_cache_bytes(int L) { return sizeof(double) * 12 * (size_t)L; }
 
 namespace {
 
@@ -19,17 +22,79 @@ namespace {
 // (u x (x_b - o)) = u . (M_p - o x G_p) with g_b = dV/dx_b (pair forces),
 // G_p = sum_{b>=p} g_b, M_p = sum_{b>=p} x_b x g_b.  Pairs on the same side
 // of the pivot contribute forces that cancel in the sum.
+constexpr int kGradThreads = 256;
+
+// Suffix sums (over b >= p) of six FP64 values, one block of residues per
+// thread, scanned across the CTA.  wtot: 8 warps x 6 doubles of scratch.
+__device__ void suffix_scan6(int L, const float* CBf, const double* CBd, const float* gbf,
+                             const double* gbd, double* GM, double* wtot) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (L + nt - 1) / nt;
+  // thread t owns residues [L - (t+1) nb, L - t nb): reversed order, so an
+  // inclusive prefix over threads is a suffix over residues
+  const int hi = L - tid * nb, lo = max(0, hi - nb);
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = hi - 1; b >= lo; --b) {
+    const double x0 = CBf ? CBf[3 * b] : CBd[3 * b], x1 = CBf ? CBf[3 * b + 1] : CBd[3 * b + 1],
+                 x2 = CBf ? CBf[3 * b + 2] : CBd[3 * b + 2];
+    const double g0 = gbf ? gbf[3 * b] : gbd[3 * b], g1 = gbf ? gbf[3 * b + 1] : gbd[3 * b + 1],
+                 g2 = gbf ? gbf[3 * b + 2] : gbd[3 * b + 2];
+    v[0] += g0; v[1] += g1; v[2] += g2;
+    v[3] += x1 * g2 - x2 * g1; v[4] += x2 * g0 - x0 * g2; v[5] += x0 * g1 - x1 * g0;
+  }
+  double incl[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) incl[q] = v[q];
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const double o = __shfl_up_sync(0xffffffffu, incl[q], off);
+      if (lane >= off) incl[q] += o;
+    }
+  }
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) wtot[warp * 6 + q] = incl[q];
+  __syncthreads();
+  double base[6] = {0, 0, 0, 0, 0, 0};
+  for (int w = 0; w < warp; ++w)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) base[q] += wtot[w * 6 + q];
+  // running suffix sum at the top of this thread's block
+  double run[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) run[q] = base[q] + incl[q] - v[q];
+  double* r = GM + (size_t)L * 6;
+  if (tid == 0)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) r[q] = 0.0;
+  for (int b = hi - 1; b >= lo; --b) {
+    const double x0 = CBf ? CBf[3 * b] : CBd[3 * b], x1 = CBf ? CBf[3 * b + 1] : CBd[3 * b + 1],
+                 x2 = CBf ? CBf[3 * b + 2] : CBd[3 * b + 2];
+    const double g0 = gbf ? gbf[3 * b] : gbd[3 * b], g1 = gbf ? gbf[3 * b + 1] : gbd[3 * b + 1],
+                 g2 = gbf ? gbf[3 * b + 2] : gbd[3 * b + 2];
+    run[0] += g0; run[1] += g1; run[2] += g2;
+    run[3] += x1 * g2 - x2 * g1; run[4] += x2 * g0 - x0 * g2; run[5] += x0 * g1 - x1 * g0;
+    double* o = GM + (size_t)b * 6;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) o[q] = run[q];
+  }
+}
+
 template <class R>
-__global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, const R* __restrict__ theta,
-                                                   double* __restrict__ E_out, R* __restrict__ grad,
-                                                   Tab<R> tb, Geom<double> geom) {
+__global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab_off,
+                                                            const R* __restrict__ theta,
+                                                            double* __restrict__ E_out,
+                                                            R* __restrict__ grad, Tab<R> tb,
+                                                            Geom<double> geom, int use_cache) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = 2 * L;
   R* X = (R*)smem;          // [4][L][3]: N, CA, C, CB
-  R* gb = X + 12 * L;       // [L][3] dV/dx_b
-  double* GM = (double*)(smem + (((size_t)sizeof(R) * 15 * L + 15) & ~(size_t)15));  // [L+1][6]
-  double* scan = GM + (size_t)6 * (L + 1);  // [warps][12] for the chain-building scan
-  __shared__ double wpart[32];
+  R* gb = X + 12 * L;       // [2][L][3] partial dV/dx_b (two halves of the a range)
+  double* GM = (double*)(smem + (((size_t)sizeof(R) * 18 * L + 15) & ~(size_t)15));  // [L+1][6]
+  double* scan = GM + (size_t)6 * (L + 1);  // [8][12] warp totals of the chain-building scan
+  double* cache = scan + 8 * 12;            // [L][12] residue transforms (if use_cache)
+  __shared__ double wpart[64];  // warp energy partials, then the suffix scan's 8 x 6 totals
   const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const R* th = theta + (size_t)v * n;
   // G(s) built in FP64 by all threads, stored in R (as the sweeps' resync)
@@ -44,15 +109,20 @@ __global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, con
           X[(q * L + i) * 3 + 2] = (R)at[q].z;
         }
       },
-      scan);
+      scan, use_cache ? cache : nullptr);
   __syncthreads();
   const R* CB = X + 9 * L;
+  // pair forces: item (b, half) sums over a in half of [0, L); each pair is
+  // visited from both ends, so no atomics are needed
   double esum = 0.0;
-  for (int b = tid; b < L; b += nt) {
+  const int half = (L + 1) / 2;
+  for (int it = tid; it < 2 * L; it += nt) {
+    const int b = it >> 1, h = it & 1;
+    const int a0 = h ? half : 0, a1 = h ? L : half;
     const V3<R> xb = v3<R>(CB[3 * b], CB[3 * b + 1], CB[3 * b + 2]);
     R gx = 0, gy = 0, gz = 0;
     R epart = 0;
-    for (int a = 0; a < L; ++a) {
+    for (int a = a0; a < a1; ++a) {
       if (a == b) continue;
       const V3<R> xa = v3<R>(CB[3 * a], CB[3 * a + 1], CB[3 * a + 2]);
       const int ra = min(a, b), rb = max(a, b);
@@ -67,35 +137,27 @@ __global__ void __launch_bounds__(256) grad_kernel(int L, long long tab_off, con
       gz += f * dlt.z;
       if (a < b) epart += e;
     }
-    gb[3 * b] = gx;
-    gb[3 * b + 1] = gy;
-    gb[3 * b + 2] = gz;
+    R* gp = gb + ((size_t)h * L + b) * 3;
+    gp[0] = gx;
+    gp[1] = gy;
+    gp[2] = gz;
     esum += (double)epart;
   }
   for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
   if ((tid & 31) == 0) wpart[tid >> 5] = esum;
   __syncthreads();
+  // fold the two halves: g_b in the first half of gb
+  for (int q = tid; q < 3 * L; q += nt) gb[q] += gb[3 * L + q];
   if (tid == 0) {
     double e = 0.0;
     for (int w = 0; w < (nt >> 5); ++w) e += wpart[w];
     E_out[v] = e;
-    // suffix sums over b >= p in FP64
-    double G0 = 0, G1 = 0, G2 = 0, M0 = 0, M1 = 0, M2 = 0;
-    double* row = GM + (size_t)L * 6;
-    row[0] = row[1] = row[2] = row[3] = row[4] = row[5] = 0.0;
-    for (int b = L - 1; b >= 0; --b) {
-      const double x0 = CB[3 * b], x1 = CB[3 * b + 1], x2 = CB[3 * b + 2];
-      const double g0 = gb[3 * b], g1 = gb[3 * b + 1], g2 = gb[3 * b + 2];
-      G0 += g0;
-      G1 += g1;
-      G2 += g2;
-      M0 += x1 * g2 - x2 * g1;
-      M1 += x2 * g0 - x0 * g2;
-      M2 += x0 * g1 - x1 * g0;
-      double* r = GM + (size_t)b * 6;
-      r[0] = G0; r[1] = G1; r[2] = G2; r[3] = M0; r[4] = M1; r[5] = M2;
-    }
   }
+  __syncthreads();
+  if (sizeof(R) == 4)
+    suffix_scan6(L, (const float*)CB, nullptr, (const float*)gb, nullptr, GM, wpart);
+  else
+    suffix_scan6(L, nullptr, (const double*)CB, nullptr, (const double*)gb, GM, wpart);
   __syncthreads();
   for (int k = tid; k < n; k += nt) {
     const int i = k >> 1, p = (k + 1) >> 1;
@@ -174,6 +236,55 @@ __global__ void best_kernel(const ProteinDev* __restrict__ prot, const int* __re
   for (int k = threadIdx.x; k < P.n; k += blockDim.x) best_theta[off + k] = theta[off + k];
 }
 
+// ---------------------------------------------------------------- replica exchange
+// One warp per candidate pair (slots j, j+1 of a ladder, j = parity mod 2):
+// swap the two states iff ln u < (1/T_j - 1/T_{j+1}) (E_j - E_{j+1}), u from
+// Philox stream 3 at (chain of slot j, round).  Energies must be current.
+template <class R>
+__global__ void exchange_kernel(const ProteinDev* __restrict__ prot,
+                                const int* __restrict__ chain_prot, int nchains, int K,
+                                const double* __restrict__ ladder, double T_scale, int parity,
+                                unsigned long long seed, unsigned long long round,
+                                R* __restrict__ theta, double* __restrict__ E,
+                                long long* __restrict__ accepted) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int a = warp;  // candidate lower slot = chain a
+  if (a >= nchains) return;
+  const ProteinDev P = prot[chain_prot[a]];
+  const int j = (a - P.chain0) % K;
+  int swap = 0;
+  const bool cand = ((j & 1) == parity) && (j + 1 < K);
+  if (cand) {
+    const int b = a + 1;
+    if (lane == 0) {
+      const uint4 w = draw_words(seed, (uint32_t)a, round, 3u);
+      const double lnu = log(uniform23d(w.x));
+      const double delta = (1.0 / (T_scale * ladder[j]) - 1.0 / (T_scale * ladder[j + 1])) *
+                           (E[a] - E[b]);
+      swap = lnu < delta;
+    }
+    swap = __shfl_sync(0xffffffffu, swap, 0);
+    if (swap) {
+      R* ta = theta + P.tors0 + (long long)(a - P.chain0) * P.n;
+      R* tb = theta + P.tors0 + (long long)(b - P.chain0) * P.n;
+      for (int k = lane; k < P.n; k += 32) {
+        const R q = ta[k];
+        ta[k] = tb[k];
+        tb[k] = q;
+      }
+      if (lane == 0) {
+        const double q = E[a];
+        E[a] = E[b];
+        E[b] = q;
+      }
+    }
+  }
+  if (lane == 0 && accepted) {
+    // each chain is written once: by its own warp (as the lower slot)
+    accepted[a] = swap;
+  }
+}
+
 // ---------------------------------------------------------------- conversions
 template <class R>
 __global__ void convert_in_kernel(const float* __restrict__ src, R* __restrict__ dst, long long n) {
@@ -219,11 +330,16 @@ template <class R>
 cudaError_t launch_grad(const ProteinDev* prot_host, int protein, int L, const R* theta, int batch,
                         double* E_out, R* grad, Tab<R> tab, Geom<R> geom, cudaStream_t st) {
   (void)protein;
-  const size_t sm = grad_smem_bytes(sizeof(R), L);
+  size_t sm = grad_smem_bytes(sizeof(R), L);
   if (batch <= 0) return cudaSuccess;
   (void)geom;
-  grad_kernel<R><<<batch, 256, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab,
-                                         ideal_geometry<double>());
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int use_cache = sm + grad_cache_bytes(L) + 1024 <= (size_t)optin ? 1 : 0;
+  if (use_cache) sm += grad_cache_bytes(L);
+  grad_kernel<R><<<batch, kGradThreads, sm, st>>>(L, prot_host->tab_off, theta, E_out, grad, tab,
+                                                  ideal_geometry<double>(), use_cache);
   return cudaGetLastError();
 }
 
@@ -267,6 +383,18 @@ cudaError_t launch_convert_out(const R* src, float* dst, long long count, cudaSt
   return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t launch_exchange(const ProteinDev* prot, const int* chain_prot, int nchains, int K,
+                            const double* ladder, double T_scale, int parity,
+                            unsigned long long seed, unsigned long long round, R* theta,
+                            double* E, long long* accepted, cudaStream_t st) {
+  const int threads = 256;
+  const long long total = (long long)nchains * 32;
+  exchange_kernel<R><<<(int)((total + threads - 1) / threads), threads, 0, st>>>(
+      prot, chain_prot, nchains, K, ladder, T_scale, parity, seed, round, theta, E, accepted);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_philox_fill(unsigned long long seed, unsigned chain, unsigned long long t0,
                                unsigned stream, long long count, uint4* words, float* z, float* u,
                                cudaStream_t st) {
@@ -286,6 +414,9 @@ cudaError_t launch_philox_fill(unsigned long long seed, unsigned chain, unsigned
   template cudaError_t launch_best<R>(const ProteinDev*, const int*, int, int, const R*, R*,        \
                                       const double*, double*, int, cudaStream_t);                  \
   template cudaError_t launch_convert_in<R>(const float*, R*, long long, cudaStream_t);            \
+  template cudaError_t launch_exchange<R>(const ProteinDev*, const int*, int, int, const double*,  \
+                                          double, int, unsigned long long, unsigned long long, R*, \
+                                          double*, long long*, cudaStream_t);                      \
   template cudaError_t launch_convert_out<R>(const R*, float*, long long, cudaStream_t);
 
 AMH_MISC_INST(float)

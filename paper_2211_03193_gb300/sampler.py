@@ -101,6 +101,16 @@ class Sampler:
     def counter(self, chain: int = 0) -> int:
         return _amh.amh_counter(self.ctx, chain)
 
+    def set_ladder(self, ladder):
+        """Parallel tempering: ladders of len(ladder) consecutive chains, slot j
+        at T * ladder[j]; None removes it."""
+        _amh.amh_set_ladder(self.ctx, ladder)
+
+    def exchange(self, T: float, parity: int, seed: int):
+        acc = np.zeros(self.n_chains, dtype=np.int64)
+        _amh.amh_exchange(self.ctx, T, parity, seed, acc)
+        return acc
+
     def launch_config(self):
         return _amh.amh_launch_config(self.ctx)
 

@@ -432,3 +432,62 @@ def test_gradient_matches_one_sided_differences(orc):
             tol = 1e-4 * (1 + abs(g[k]))
             assert lo - tol <= g[k] <= hi + tol, (k, g[k], left, right)
         assert g[0] == 0.0 and g[-1] == 0.0
+
+
+# ---------------------------------------------------------------- parallel tempering
+def _lattice_setup(orc, K=3, L=4, seed=21):
+    import itertools
+    prot = small_problem(L, seed=seed)
+    P = orc.Problem(L, prot.p, prot.edges)
+    n = 2 * L
+    q = 2 * np.pi / K
+    live = list(range(1, n - 1))
+    grid = np.array(list(itertools.product(range(K), repeat=len(live))))
+    S = np.zeros((grid.shape[0], n))
+    S[:, live] = wrapd(grid * q)
+    E = P.energies(S)
+    gidx = (np.mod(grid, K) * K ** np.arange(len(live) - 1, -1, -1)).sum(1)
+    order = np.argsort(gidx)
+    return P, prot, n, q, live, E[order]
+
+
+def _state_index(S, live, q, K):
+    m = np.mod(np.rint(S[:, live] / q).astype(np.int64), K)
+    return (m * K ** np.arange(len(live) - 1, -1, -1)).sum(1)
+
+
+@pytest.mark.slow
+def test_parallel_tempering_keeps_each_slot_at_its_boltzmann_law(orc):
+    """Replica exchange (Metropolis rule for swapping replicas of exp(-E/T)):
+    with global sweeps and exchanges alternating, every ladder slot samples
+    exp(-E/T_j)/Z_j; a sign error in the exchange rule would heat the cold
+    slots.  Exact laws by enumerating the 3^6 lattice states."""
+    K = 3
+    P, prot, n, q, live, Es = _lattice_setup(orc, K=K)
+    T0 = float(np.std(Es)) / 2
+    ladder = np.array([1.0, 1.6, 2.6, 4.2])
+    Kl = len(ladder)
+    S = np.zeros((Kl, n))
+    rounds = 60000
+    counts = np.zeros((Kl, K ** len(live)))
+    for r in range(rounds):
+        for j in range(Kl):
+            S[j], _, _ = P.run(S[j], orc.GLOBAL, 0, T0 * ladder[j], 1.5, r * n, n, 11, j, lattice_K=K)
+        E = P.energies(S)
+        E, S, _ = orc.exchange(E, S, Kl, ladder, T0, r % 2, 13, r)
+        if r >= 500:
+            idx = _state_index(S, live, q, K)
+            counts[np.arange(Kl), idx] += 1
+    for j in range(Kl):
+        w = np.exp(-(Es - Es.min()) / (T0 * ladder[j]))
+        pi = w / w.sum()
+        hist = counts[j] / counts[j].sum()
+        mean_exact = float(pi @ Es)
+        mean_obs = float(hist @ Es)
+        sd = float(np.sqrt(pi @ (Es - mean_exact) ** 2))
+        tv = 0.5 * np.abs(hist - pi).sum()
+        tv_noise = 0.5 * np.sum(np.sqrt(2 * pi * (1 - pi) / (np.pi * counts[j].sum())))
+        print("slot", j, "mean", mean_obs, mean_exact, "sd", sd, "tv", tv, "noise", tv_noise)
+        assert abs(mean_obs - mean_exact) < 0.05 * sd, (j, mean_obs, mean_exact, sd)
+        # consecutive rounds are correlated: allow twice the independent-sample noise
+        assert tv < 2.0 * tv_noise, (j, tv, tv_noise)
