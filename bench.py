@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target measurement")
+    ap.add_argument("--experiment", default="", choices=["", "schemes", "forms", "batched"],
+                    help="schemes: AMH vs plain MH vs MH with noisy restarts (L=150); forms: "
+                         "batched FP32 vs one-chain FP64 (L=300); batched: 64 uneven proteins")
     ap.add_argument("--chains-per-cta", type=int, default=0,
                     help="global-sweep chains per CTA (0 = autotuned)")
     ap.add_argument("--threads", type=int, default=0, help="global-sweep threads per CTA")
@@ -265,6 +268,120 @@ def time_to_target(stream_cls=None):
             "gpu_sweeps": s + 1, "reached": reached,
             "speedup": cpu_s / gpu_s if reached else None,
             "note": "CPU: FP64 oracle, one chain per core, wall time of the 10 parallel runs"}
+
+
+def run_schemes():
+    """The L=150 workload's comparison (Sec. 3, Fig. 3A protocol on synthetic
+    data): 1024 chains, 200k proposals each, T 2.0 -> 0.05, sigma 10 -> 4 deg;
+    AMH (10 local d=8 : 1 global), plain MH (global only) and MH with noisy
+    restarts (N(0, 30 deg) kicks every 20k proposals).  Prints one JSON line
+    per scheme with the chains' best energies."""
+    import torch
+    from paper_2211_03193_gb300 import synth
+    from paper_2211_03193_gb300.sampler import Sampler, Schedule, run_schedule
+    w = workload("amh_L150_c1024")
+    L, n, chains = w["L"], w["n"], w["chains"]
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    tors = synth.random_torsions(chains, L, seed=w["start_seed"])
+    total = w["proposals"] // n
+    schemes = {
+        "amh": dict(n_local=10, n_global=1, noisy_every=0),
+        "amh_80g_20l_d5": dict(n_local=20, n_global=80, noisy_every=0, window=5),
+        "mh": dict(n_local=0, n_global=1, noisy_every=0),
+        "mh_noisy_restarts": dict(n_local=0, n_global=1, noisy_every=max(1, 20000 // n)),
+    }
+    for name, kw in schemes.items():
+        kw = dict(kw)
+        win = kw.pop("window", w["window"])
+        sched = Schedule(total_sweeps=total, window=win, T0=w["T0"], T1=w["T1"],
+                         sigma0_deg=10.0, sigma1_deg=4.0, seed=3, noisy_sd_deg=30.0, **kw)
+        stream = torch.cuda.Stream()
+        with Sampler(prot, chains, tors, stream=stream) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                run_schedule(s, sched)
+            E = s.energy()
+            bE = s.state()[2]
+            dt = time.perf_counter() - t0
+        print(json.dumps({"experiment": "schemes", "scheme": name, "L": L, "chains": chains,
+                          "proposals_per_chain": total * n, "seconds": dt,
+                          "best_of_chains": float(bE.min()),
+                          "median_chain_best": float(np.median(bE)),
+                          "median_final_energy": float(np.median(E))}))
+
+
+def run_forms():
+    """The batched FP32 form against the plain FP64 form (one chain per
+    launch) on the same GPU, L=300: proposals/s of one AMH cycle."""
+    import torch
+    from paper_2211_03193_gb300 import _amh, synth
+    from paper_2211_03193_gb300.sampler import Sampler
+    w = workload("amh_L300_c1024")
+    L, n = w["L"], w["n"]
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    sched = schedule_for(w, seed=1)
+    for label, chains, prec in (("fp32_batched_1024", 1024, 32), ("fp32_one_chain", 1, 32),
+                                ("fp64_one_chain", 1, 64)):
+        tors = synth.random_torsions(chains, L, seed=w["start_seed"])
+        stream = torch.cuda.Stream()
+        with Sampler(prot, chains, tors, precision=prec, stream=stream) as s:
+            def cycle():
+                for q in range(w["cycle"]):
+                    mode, T, sigma = sched.params(q)
+                    _amh.amh_sweeps(s.ctx, mode, w["window"], T, sigma, 1, 1, None)
+            with torch.cuda.stream(stream):
+                cycle()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                cycle()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        print(json.dumps({"experiment": "forms", "form": label, "L": L, "chains": chains,
+                          "precision": prec, "ms_per_cycle": ms,
+                          "proposals_per_s": w["cycle"] * n * chains / (ms / 1000.0)}))
+
+
+def run_batched():
+    """64 proteins with L uniform in [50, 400], 256 chains each, one context:
+    one AMH cycle (10 local + 1 global sweep per chain) through the persistent
+    work queue; proposals/s over all chains."""
+    import torch
+    from paper_2211_03193_gb300 import _amh, synth
+    from paper_2211_03193_gb300.sampler import Sampler
+    w = dict(synth.WORKLOADS["amh_batched_64prot"])
+    Ls = synth.uneven_lengths(w["nproteins"], w["Lmin"], w["Lmax"], seed=3)
+    prots = [synth.make_protein(L, seed=w["seed"] + i) for i, L in enumerate(Ls)]
+    chains = [w["chains"]] * len(Ls)
+    tors = np.concatenate([synth.random_torsions(w["chains"], L, seed=w["start_seed"] + i).ravel()
+                           for i, L in enumerate(Ls)])
+    stream = torch.cuda.Stream()
+    with Sampler(prots, chains, tors, resync_every=w["resync_every"], stream=stream) as s:
+        def cycle():
+            for q in range(11):
+                mode = 0 if q < 10 else 1
+                _amh.amh_sweeps(s.ctx, mode, w["window"], 1.0, math.radians(10.0), 1, 1, None)
+        with torch.cuda.stream(stream):
+            cycle()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            cycle()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        C, thr, D = s.launch_config()
+    props = sum(11 * 2 * L * w["chains"] for L in Ls)
+    print(json.dumps({"experiment": "batched", "proteins": len(Ls), "chains": sum(chains),
+                      "L_range": [min(Ls), max(Ls)], "ms_per_cycle": ms,
+                      "proposals_per_s": props / (ms / 1000.0), "chains_per_cta": C,
+                      "threads_per_cta": thr}))
 
 
 def run_reference(args):
@@ -472,6 +589,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.experiment:
+        {"schemes": run_schemes, "forms": run_forms, "batched": run_batched}[args.experiment]()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

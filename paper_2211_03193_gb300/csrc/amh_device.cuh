@@ -93,12 +93,25 @@ struct Geom {
   R cbT_c, cbT_s;                // CB improper dihedral N-C-CA-CB (cos, sin)
 };
 
-// NeRF: atom D bonded to C with the given (-b cos a, b sin a) and dihedral
-// A-B-C-D of cosine ct and sine st.
+// Normalisation for short builds (window-local coordinates): FP32 uses the
+// approximate MUFU reciprocal square root; errors cannot accumulate over a
+// window of a few residues.
 template <class R>
+__device__ __forceinline__ V3<R> unit_short(V3<R> a) {
+  return a * rsqrt_(dot(a, a));
+}
+template <>
+__device__ __forceinline__ V3<float> unit_short<float>(V3<float> a) {
+  return a * rsqrt_ftz(dot(a, a));
+}
+
+// NeRF: atom D bonded to C with the given (-b cos a, b sin a) and dihedral
+// A-B-C-D of cosine ct and sine st.  SHORT selects the short-build
+// normalisation.
+template <class R, bool SHORT = false>
 __device__ __forceinline__ V3<R> place(V3<R> A, V3<R> B, V3<R> C, R pc, R ps, R ct, R st) {
-  V3<R> bc = unit(C - B);
-  V3<R> nrm = unit(cross(B - A, bc));
+  V3<R> bc = SHORT ? unit_short(C - B) : unit(C - B);
+  V3<R> nrm = SHORT ? unit_short(cross(B - A, bc)) : unit(cross(B - A, bc));
   V3<R> m = cross(nrm, bc);
   R py = ps * ct, pz = ps * st;
   return v3<R>(C.x + bc.x * pc + m.x * py + nrm.x * pz, C.y + bc.y * pc + m.y * py + nrm.y * pz,
@@ -114,23 +127,23 @@ __device__ __forceinline__ void first_residue(const Geom<R>& g, V3<R>& N, V3<R>&
 }
 
 // Next residue from the previous one: psi_i, omega = 180 deg, phi_{i+1}.
-template <class R>
+template <class R, bool SHORT = false>
 __device__ __forceinline__ void next_residue(const Geom<R>& g, V3<R>& N, V3<R>& CA, V3<R>& C,
                                              R psi, R phi) {
   R sp, cp, sf, cf;
   sincos_(psi, &sp, &cp);
   sincos_(phi, &sf, &cf);
-  V3<R> N1 = place(N, CA, C, g.pN_c, g.pN_s, cp, sp);
-  V3<R> CA1 = place(CA, C, N1, g.pCA_c, g.pCA_s, R(-1), R(0));
-  V3<R> C1 = place(C, N1, CA1, g.pC_c, g.pC_s, cf, sf);
+  V3<R> N1 = place<R, SHORT>(N, CA, C, g.pN_c, g.pN_s, cp, sp);
+  V3<R> CA1 = place<R, SHORT>(CA, C, N1, g.pCA_c, g.pCA_s, R(-1), R(0));
+  V3<R> C1 = place<R, SHORT>(C, N1, CA1, g.pC_c, g.pC_s, cf, sf);
   N = N1;
   CA = CA1;
   C = C1;
 }
 
-template <class R>
+template <class R, bool SHORT = false>
 __device__ __forceinline__ V3<R> cbeta(const Geom<R>& g, V3<R> N, V3<R> CA, V3<R> C) {
-  return place(N, C, CA, g.pCB_c, g.pCB_s, g.cbT_c, g.cbT_s);
+  return place<R, SHORT>(N, C, CA, g.pCB_c, g.pCB_s, g.cbT_c, g.cbT_s);
 }
 
 // Affine map x -> M x + t (M row-major), stored as 12 values.

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
             Pax = N;
             Qax = CA;
             for (int rr = lo;; ++rr) {
-              const V3<R> cb = cbeta(a.geom, N, CA, Cc);
+              const V3<R> cb = cbeta<R, true>(a.geom, N, CA, Cc);
               const int j = rr - lo;
               cbs[(j * 3 + 0) * nt + tid] = cb.x;
               cbs[(j * 3 + 1) * nt + tid] = cb.y;
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                 }
               }
               if (rr == hi) break;
-              next_residue(a.geom, N, CA, Cc, th_s[(2 * rr + 1) * Gc + c],
-                           th_s[(2 * rr + 2) * Gc + c]);
+              next_residue<R, true>(a.geom, N, CA, Cc, th_s[(2 * rr + 1) * Gc + c],
+                                    th_s[(2 * rr + 2) * Gc + c]);
             }
             const Aff<R> A = rotation(Pax, Qax, wrap_angle(thn - th));
             typename AccT<R>::T acc = 0;

@@ -150,7 +150,9 @@ class Schedule:
     sigma_s linear from sigma0 to sigma1 (degrees) over the S sweeps; both
     constant within a sweep.  n_local = 0 gives plain MH; noisy_every > 0
     adds a Gaussian kick of noisy_sd_deg to every torsion every that many
-    sweeps (MH with noisy restarts)."""
+    sweeps (MH with noisy restarts).  windows (optional) cascades several
+    localization radii (Sec. 2.2: "one can cascade multiple localization
+    ranges"): local sweep j of a cycle uses windows[j % len(windows)]."""
     total_sweeps: int
     n_local: int = 10
     n_global: int = 1
@@ -162,6 +164,13 @@ class Schedule:
     seed: int = 1
     noisy_every: int = 0
     noisy_sd_deg: float = 30.0
+    windows: tuple | None = None
+
+    def window_of(self, s: int) -> int:
+        if not self.windows:
+            return self.window
+        j = s % (self.n_local + self.n_global)
+        return self.windows[j % len(self.windows)]
 
     def params(self, s: int):
         S = max(self.total_sweeps - 1, 1)
@@ -181,7 +190,8 @@ def run_schedule(sampler: Sampler, sched: Schedule, s0: int = 0, s1: int | None 
     total = np.zeros(sampler.n_chains, dtype=np.int64)
     for s in range(s0, s1):
         mode, T, sigma = sched.params(s)
-        acc = sampler.sweeps(mode, sched.window, T, sigma, 1, sched.seed, accepted=on_sweep is not None)
+        acc = sampler.sweeps(mode, sched.window_of(s), T, sigma, 1, sched.seed,
+                             accepted=on_sweep is not None)
         if acc is not None:
             total += acc
         if sched.noisy_every and (s + 1) % sched.noisy_every == 0:
@@ -203,8 +213,40 @@ def capture_schedule(sampler: Sampler, sched: Schedule, s0: int, s1: int, stream
     with torch.cuda.graph(g, stream=stream):
         for s in range(s0, s1):
             mode, T, sigma = sched.params(s)
-            _amh.amh_sweeps(sampler.ctx, mode, sched.window, T, sigma, 1, sched.seed, None)
+            _amh.amh_sweeps(sampler.ctx, mode, sched.window_of(s), T, sigma, 1, sched.seed, None)
             if sched.noisy_every and (s + 1) % sched.noisy_every == 0:
                 _amh.amh_noisy_restart(sampler.ctx, math.radians(sched.noisy_sd_deg),
                                        sched.seed * 1000003 + s)
     return g
+
+
+def restart_from_best(sampler: Sampler, sched: Schedule, runs: int = 10, on_run=None):
+    """Sec. 2.3's protocol: the whole schedule is run `runs` times; each run
+    starts every chain from the lowest-energy state it has seen (its best
+    state at global-sweep ends).  While runs keep lowering the best energy the
+    step sigma follows sched (10 -> 4 deg); after F runs without a new lowest
+    energy it follows 10/F -> 1/F deg.  "Lower" is judged on the lowest
+    energy over all chains.  Returns the best energy after each run."""
+    import dataclasses
+    history = []
+    best = float(np.min(sampler.state()[2]))
+    failures = 0
+    for r in range(runs):
+        if failures:
+            sig = (10.0 / failures, 1.0 / failures)
+        else:
+            sig = (sched.sigma0_deg, sched.sigma1_deg)
+        sr = dataclasses.replace(sched, sigma0_deg=sig[0], sigma1_deg=sig[1],
+                                 seed=sched.seed + 7919 * r)
+        if r:
+            sampler.set_state(sampler.state()[3])  # every chain from its best state
+        run_schedule(sampler, sr)
+        now = float(np.min(sampler.state()[2]))
+        if now < best:
+            best = now
+        else:
+            failures += 1
+        history.append(best)
+        if on_run is not None:
+            on_run(r, best, sig)
+    return history

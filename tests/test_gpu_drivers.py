@@ -93,3 +93,46 @@ def test_graph_replay_equals_eager_schedule(env, noisy):
         assert s.counter(0) == 16 * 2 * L
     for a, b in zip(want, got):
         assert np.array_equal(a, b)
+
+
+def test_cascaded_windows_follow_the_schedule(env, orc):
+    """Local sweep j of a cycle uses windows[j % len(windows)]: the GPU run
+    equals the oracle's sweep-by-sweep replay with those windows (FP64)."""
+    torch, sampler, autograd = env
+    L, chains = 18, 2
+    prot = synth.make_protein(L, seed=840)
+    tors = synth.random_torsions(chains, L, seed=841)
+    sched = sampler.Schedule(total_sweeps=8, n_local=3, n_global=1, windows=(4, 8, 12), T0=1.0,
+                             T1=0.5, seed=6)
+    n = 2 * L
+    P = orc.Problem(L, prot.p, prot.edges)
+    with sampler.Sampler(prot, chains, tors, precision=64) as s:
+        sampler.run_schedule(s, sched)
+        th = s.torsions()
+    for c in range(chains):
+        st = tors[c].astype(np.float64)
+        for q in range(8):
+            mode, T, sigma = sched.params(q)
+            st, _, _ = P.run(st, orc.LOCAL if mode == 0 else orc.GLOBAL, sched.window_of(q), T,
+                             sigma, q * n, n, 6, c)
+        assert np.allclose(th[c], st, atol=1e-6)
+    assert [sched.window_of(q) for q in range(3)] == [4, 8, 12]
+
+
+def test_restart_from_best_protocol(env):
+    torch, sampler, autograd = env
+    L, chains = 24, 64
+    prot = synth.make_protein(L, seed=850)
+    tors = synth.random_torsions(chains, L, seed=851)
+    sched = sampler.Schedule(total_sweeps=11, n_local=10, n_global=1, T0=1.0, T1=0.2, seed=2)
+    seen = []
+    with sampler.Sampler(prot, chains, tors) as s:
+        E0 = float(s.state()[2].min())
+        hist = sampler.restart_from_best(s, sched, runs=4,
+                                         on_run=lambda r, b, sig: seen.append(sig))
+        assert s.counter(0) == 4 * 11 * 2 * L
+    assert all(b2 <= b1 for b1, b2 in zip(hist, hist[1:]))
+    assert hist[-1] <= E0
+    assert seen[0] == (10.0, 4.0)
+    for (a, b) in seen[1:]:
+        assert (a, b) == (10.0, 4.0) or abs(a / b - 10.0) < 1e-12
