@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--chains-per-cta", type=int, default=0,
                     help="global-sweep chains per CTA (0 = autotuned)")
     ap.add_argument("--threads", type=int, default=0, help="global-sweep threads per CTA")
+    ap.add_argument("--texture", type=int, default=0,
+                    help="table entries: 0 default (texture when it fits), 1 texture, 2 loads")
     ap.add_argument("--stage", type=int, default=0,
                     help="table rows: 0 tuned, 1 staged in shared memory, 2 through L1")
     return ap.parse_args()
@@ -450,7 +452,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
-                   stage_table=args.stage)
+                   stage_table=args.stage, table_texture=args.texture)
     C, thr, D = samp.launch_config()
     sched = schedule_for(w, seed=1 + rank)
     cyc = w["cycle"]
@@ -558,7 +560,9 @@ def run_ours(args):
             "frac": achieved / peak_tf, "traffic": captured_traffic(args.workload, (C, thr, D)),
             "kernel": "global_kernel<float,%d,%s> (global sweep, %d threads/CTA%s)" % (
                 C, "true" if D else "false", thr,
-                ", table rows staged %d deep" % D if D else ", table rows through L1"),
+                ", table rows staged %d deep" % D if D else
+                (", table entries through the texture path" if args.texture != 2
+                 else ", table entries through L1 loads")),
             "launch_ms": g_ms, "pair_evals_per_launch": evals_glob_launch,
             "flop_per_eval": FLOP_PER_EVAL,
             "peak_basis": "%d SMs x %d FP32 lanes x 2 (FMA) x %.0f MHz (%s max clock)" % (

@@ -73,6 +73,11 @@ typedef struct {
                               (AMH_EINVAL if impossible: needs precision 32
                               and 4 or 8 chains per CTA), 2: never staged
                               (read through the L1 cache). */
+  int table_texture;       /* precision 32, global sweeps: 0 = fetch table entries
+                              through a 1-D texture (32-bit indices) when the
+                              table fits the device's 1-D texture limit, else
+                              global loads (default); 1 = texture (AMH_EINVAL if
+                              it does not fit); 2 = global loads. */
   void* stream;            /* cudaStream_t; NULL = the legacy default stream */
 } amh_options;
 

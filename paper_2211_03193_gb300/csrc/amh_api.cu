@@ -50,6 +50,7 @@ struct amh_ctx {
   // launch configuration
   int C = 8, threads = 256, grid_global = 1;
   int stage_depth = 0;  // > 0: global sweeps stage table rows through shared memory
+  cudaTextureObject_t tex = 0;  // FP32 table as a 1-D texture (0: not used)
   double* ladder = nullptr;  // parallel tempering: per-slot temperature factors
   int ladder_K = 0;
   unsigned long long xround = 0;  // exchange rounds so far (Philox counter)
@@ -113,6 +114,7 @@ Tab<R> make_tab(const amh_ctx* ctx) {
   t.k1 = (R)(1.0 / ctx->w / (ctx->B - 1));
   t.k2 = (R)(-ctx->c0 / ctx->w / (ctx->B - 1));
   t.Bp = ctx->Bp;
+  t.tex = ctx->tex;
   return t;
 }
 
@@ -434,6 +436,25 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
                                (R*)ctx->table, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   cudaFree(tmp);
+  if (ctx->precision == 32 && ctx->opt.table_texture != 2) {
+    // the FP32 table also as a 1-D linear texture of float2 entries
+    const size_t entries = (size_t)ctx->rows_total * ctx->Bp;
+    cudaResourceDesc rd;
+    memset(&rd, 0, sizeof(rd));
+    rd.resType = cudaResourceTypeLinear;
+    rd.res.linear.devPtr = ctx->table;
+    rd.res.linear.desc = cudaCreateChannelDesc<float2>();
+    rd.res.linear.sizeInBytes = entries * sizeof(float2);
+    cudaTextureDesc td;
+    memset(&td, 0, sizeof(td));
+    td.readMode = cudaReadModeElementType;
+    int maxw = 0;
+    CK(ctx, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, ctx->device));
+    if (entries <= (size_t)maxw && entries < (1ull << 31))
+      CK(ctx, cudaCreateTextureObject(&ctx->tex, &rd, &td, nullptr));
+    else if (ctx->opt.table_texture == 1)
+      return set_err(ctx, AMH_EINVAL, "the table exceeds the 1-D texture limit");
+  }
   // state
   const size_t tb = sizeof(R) * (size_t)ctx->tors_total;
   CK(ctx, cudaMalloc(&ctx->theta, tb));
@@ -522,6 +543,7 @@ void free_ctx(amh_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->tex) cudaDestroyTextureObject(ctx->tex);
   void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
                   ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
                   ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder};
@@ -552,6 +574,7 @@ void amh_options_default(amh_options* opt) {
   opt->lattice_K = 0;
   opt->table_is_neglog = 0;
   opt->stage_table = 0;
+  opt->table_texture = 0;
   opt->stream = nullptr;
 }
 
@@ -579,6 +602,8 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   if (o.threads_per_cta != 0 && o.threads_per_cta != 128 && o.threads_per_cta != 256 &&
       o.threads_per_cta != 512)
     return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 128, 256 or 512");
+  if (o.table_texture < 0 || o.table_texture > 2)
+    return set_err(nullptr, AMH_EINVAL, "table_texture must be 0, 1 or 2");
   if (o.stage_table < 0 || o.stage_table > 2)
     return set_err(nullptr, AMH_EINVAL, "stage_table must be 0, 1 or 2");
   if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)

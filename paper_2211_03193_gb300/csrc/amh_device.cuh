@@ -379,6 +379,7 @@ struct Tab {
   R umax;                                     // B - 1
   R k1, k2;                                   // inv_w / umax, off / umax
   int Bp;
+  cudaTextureObject_t tex;                    // FP32: the same entries as a 1-D texture (or 0)
 };
 
 // floor(u) for 0 <= u < 2^22 as (integer, float): adding 2^23 rounded down
@@ -434,6 +435,17 @@ __device__ __forceinline__ R pair_term_slope(const typename Vec2<R>::T* __restri
   const typename Vec2<R>::T v = __ldg(row + j);
   *slope = (u0 >= R(0) && u0 < tb.umax) ? v.y * tb.inv_w : R(0);
   return fma(u - jf, v.y, v.x);
+}
+
+// The same term fetched through the texture path from a 32-bit entry index
+// (row_e: index of the row's first entry): the texture unit forms the
+// address, so a term costs one integer add instead of 64-bit arithmetic.
+__device__ __forceinline__ float pair_term_tex(int row_e, float d, const Tab<float>& tb) {
+  const float us = __saturatef(fmaf(d, tb.k1, tb.k2));
+  const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
+  const float t = fmaf(us, tb.umax, 8388608.0f - f);
+  const float2 v = tex1Dfetch<float2>(tb.tex, row_e - 0x4B000000 + __float_as_int(f));
+  return fmaf(t, v.y, v.x);
 }
 
 // The same term read from a row staged in shared memory (32-bit address:

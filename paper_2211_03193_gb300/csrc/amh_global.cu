@@ -211,7 +211,7 @@ __device__ __forceinline__ void store_aff(R* dst, const Aff<R>& A) {
 }
 
 // Straddle-block Delta-E (moving side [m0, m1), fixed side [f0, f1)).
-template <class R, int C, bool FUSED>
+template <class R, int C, bool FUSED, bool TEX>
 __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, int L, int m0,
                            int m1, int f0, int f1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -242,23 +242,37 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     // rows of the pairs (f, m): contiguous in f when m < f; when f < m,
     // r(f+1, m) - r(f, m) = L - f - 2
     const bool mfirst = m < fb;
-    const auto* row =
-        tb.E + tab_off + (long long)(mfirst ? row_of(L, m, fb) : row_of(L, fb, m)) * tb.Bp;
+    const int r0 = mfirst ? row_of(L, m, fb) : row_of(L, fb, m);
+    const auto* row = tb.E + tab_off + (long long)r0 * tb.Bp;
+    int rowe = (int)tab_off + r0 * tb.Bp;  // entry index (texture path)
     int step = mfirst ? 1 : L - fb - 2;
     const int dstep = mfirst ? 0 : -1;
 #pragma unroll 4
     for (int f = fb; f < fe; ++f) {
       const V3<R> xf = s.cb(f, c);
-      const R e0 = pair_term(row, dist_(xf, xm), tb);
-      const R e1 = pair_term(row, dist_(xf, y1), tb);
+      R e0, e1, e2 = 0, e21 = 0;
+      if constexpr (TEX) {
+        e0 = pair_term_tex(rowe, dist_(xf, xm), tb);
+        e1 = pair_term_tex(rowe, dist_(xf, y1), tb);
+        if (FUSED) {
+          e2 = pair_term_tex(rowe, dist_(xf, y2), tb);
+          e21 = pair_term_tex(rowe, dist_(xf, y21), tb);
+        }
+        rowe += step * tb.Bp;
+      } else {
+        e0 = pair_term(row, dist_(xf, xm), tb);
+        e1 = pair_term(row, dist_(xf, y1), tb);
+        if (FUSED) {
+          e2 = pair_term(row, dist_(xf, y2), tb);
+          e21 = pair_term(row, dist_(xf, y21), tb);
+        }
+        row += (long long)step * tb.Bp;
+      }
       acc1 += e1 - e0;
       if (FUSED) {
-        const R e2 = pair_term(row, dist_(xf, y2), tb);
-        const R e21 = pair_term(row, dist_(xf, y21), tb);
         acc2 += e2 - e0;
         acc21 += e21 - e1;
       }
-      row += (long long)step * tb.Bp;
       step += dstep;
     }
   }
@@ -586,11 +600,23 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
                 : pair_block_staged<C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1,
                                               a.stage_depth, par, a.err);
       if (!ok) *(volatile int*)abort_flag = 1;
+    } else if constexpr (sizeof(R) == 4) {
+      if (a.tab.tex) {
+        if (fused)
+          pair_block<R, C, true, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+        else
+          pair_block<R, C, false, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+      } else {
+        if (fused)
+          pair_block<R, C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+        else
+          pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+      }
     } else {
       if (fused)
-        pair_block<R, C, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+        pair_block<R, C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
       else
-        pair_block<R, C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+        pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
     }
     __syncthreads();
     if (*(volatile int*)abort_flag) break;  // a staging wait gave up: stop (flagged)

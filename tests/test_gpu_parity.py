@@ -163,12 +163,14 @@ def test_energy_uneven_proteins_and_64_bins(amh, orc):
 
 
 # ---------------------------------------------------------------- global sweeps
-@pytest.mark.parametrize("precision,C,stage,threads", [
-    (64, 1, 2, 256), (64, 4, 2, 256), (32, 8, 2, 256), (32, 2, 2, 256), (32, 1, 2, 128),
-    (32, 8, 1, 512), (32, 4, 1, 256), (32, 8, 1, 128)])
-def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads):
+@pytest.mark.parametrize("precision,C,stage,threads,tex", [
+    (64, 1, 2, 256, 0), (64, 4, 2, 256, 0), (32, 8, 2, 256, 2), (32, 2, 2, 256, 2),
+    (32, 1, 2, 128, 2), (32, 8, 1, 512, 2), (32, 4, 1, 256, 2), (32, 8, 1, 128, 2),
+    (32, 8, 2, 512, 1), (32, 4, 2, 256, 1), (32, 2, 2, 256, 0)])
+def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads, tex):
     """stage 1: table rows staged in shared memory by bulk async copies;
-    stage 2: read through L1."""
+    stage 2: read through L1; tex 1: entries fetched through a texture, 2:
+    global loads, 0: the default (texture)."""
     L, chains = 33, 11
     prot = synth.make_protein(L, seed=300)
     tors = synth.random_torsions(chains, L, seed=301)
@@ -176,7 +178,7 @@ def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads):
     steps = 3 * n + 7  # ragged: ends mid-sweep, with an odd leftover
     T, sigma, seed = 0.8, 25 * DEG, 99
     with amh.Sampler(prot, chains, tors, precision=precision, chains_per_cta=C,
-                     threads_per_cta=threads, stage_table=stage,
+                     threads_per_cta=threads, stage_table=stage, table_texture=tex,
                      trace_chains=chains, trace_capacity=steps, resync_every=50) as s:
         assert s.launch_config()[2] == (0 if stage == 2 else s.launch_config()[2])
         if stage == 1:
