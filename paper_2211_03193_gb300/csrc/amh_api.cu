@@ -492,6 +492,9 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   return check_err_flag(ctx);
 }
 
+// Most chains per CTA of a local sweep.
+constexpr int kLocalMaxChains = 32;
+
 template <class R>
 amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma, long long steps,
                       int are_sweeps, unsigned long long seed) {
@@ -511,16 +514,24 @@ amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma
     const int ncol = std::max(4 * h, 1);
     const int cnt = (ctx->nmax + ncol - 1) / ncol;
     int q = 0;
-    while (q < 5 && (2 << q) * cnt <= 256) ++q;  // Gc = 2^q with Gc * cnt <= 256
-    const int Gc = 1 << q;
+    while (q < 5 && (2 << q) <= kLocalMaxChains && (2 << q) * cnt <= 256) ++q;
+    // 256 threads (measured faster than one thread per window of a colour:
+    // the idle lanes cost less than the extra CTAs); fewer chains per CTA,
+    // then fewer threads, until shared memory fits
+    const size_t room = ctx->smem_optin - kStaticSmemMargin;
     int threads = 256;
-    size_t sm = local_smem_bytes<R>(ctx->nmax, Gc, threads, window);
-    while (sm > ctx->smem_optin - kStaticSmemMargin && threads > 32) {
-      threads /= 2;
-      sm = local_smem_bytes<R>(ctx->nmax, Gc, threads, window);
+    size_t sm = 0;
+    for (; q >= 0; --q) {
+      threads = 256;
+      for (;;) {
+        sm = local_smem_bytes<R>(ctx->nmax, 1 << q, threads, window);
+        if (sm <= room || threads == 32) break;
+        threads = std::max(32, (threads / 2 + 31) / 32 * 32);
+      }
+      if (sm <= room) break;
     }
-    if (sm > ctx->smem_optin - kStaticSmemMargin)
-      return set_err(ctx, AMH_EINVAL, "window too large for shared memory");
+    if (q < 0 || sm > room) return set_err(ctx, AMH_EINVAL, "window too large for shared memory");
+    const int Gc = 1 << q;
     a.groups = ctx->lgroups_d[q];
     a.ngroups = ctx->nlgroups[q];
     const int per_sm = std::max(1, std::min((int)(ctx->smem_optin / std::max<size_t>(sm, 1)),

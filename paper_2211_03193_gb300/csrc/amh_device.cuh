@@ -79,6 +79,18 @@ __device__ __forceinline__ double dist_(V3<double> a, V3<double> b) {
   return sqrt(dot(d, d));
 }
 
+// Distance through one approximate square root (sqrt.approx, relative error
+// of the order of 2^-23, sqrt(0) = 0): the pair loops of the sweeps.  FP64
+// falls back to sqrt.
+__device__ __forceinline__ float dist_fast(V3<float> a, V3<float> b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d2));
+  return r;
+}
+__device__ __forceinline__ double dist_fast(V3<double> a, V3<double> b) { return dist_(a, b); }
+
 // ------------------------------------------------------------------ geometry
 // Ideal geometry as (-bond cos(angle), bond sin(angle)) pairs, filled on
 // the host in double precision (see amh.h for the values).
@@ -200,6 +212,35 @@ __device__ __forceinline__ Aff<R> compose(const Aff<R>& B, const Aff<R>& A) {
   return r;
 }
 
+// Four values at a 4-value boundary (one 16-byte shared load in FP32): a
+// padded point, or a third of an affine map.
+template <class R>
+struct alignas(4 * sizeof(R)) Pt4 {
+  R x, y, z, w;
+};
+
+// An affine map stored as three Pt4: m[0..3], m[4..7], (m[8], t).
+template <class R>
+__device__ __forceinline__ Aff<R> aff_load4(const Pt4<R>* q) {
+  const Pt4<R> a = q[0], b = q[1], d = q[2];
+  Aff<R> A;
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.t[0] = d.y; A.t[1] = d.z; A.t[2] = d.w;
+  return A;
+}
+
+template <class R>
+__device__ __forceinline__ void aff_store4(Pt4<R>* q, const Aff<R>& A) {
+  Pt4<R> a, b, d;
+  a.x = A.m[0]; a.y = A.m[1]; a.z = A.m[2]; a.w = A.m[3];
+  b.x = A.m[4]; b.y = A.m[5]; b.z = A.m[6]; b.w = A.m[7];
+  d.x = A.m[8]; d.y = A.t[0]; d.z = A.t[1]; d.w = A.t[2];
+  q[0] = a;
+  q[1] = b;
+  q[2] = d;
+}
+
 template <class R>
 __device__ __forceinline__ Aff<R> identity_map() {
   Aff<R> A;
@@ -220,25 +261,27 @@ __device__ __forceinline__ Aff<R> identity_map() {
 
 // Orthonormal frame of a residue (columns e1 = CA->C, e2 = CA->N made
 // orthogonal to e1, e3 = e1 x e2) as the rotation part of an affine map.
-__device__ __forceinline__ void residue_frame(V3<double> N, V3<double> CA, V3<double> C,
-                                              double Q[9]) {
-  const V3<double> e1 = unit(C - CA);
-  V3<double> v = N - CA;
+template <class R>
+__device__ __forceinline__ void residue_frame(V3<R> N, V3<R> CA, V3<R> C, R Q[9]) {
+  const V3<R> e1 = unit(C - CA);
+  V3<R> v = N - CA;
   v = v - e1 * dot(v, e1);
-  const V3<double> e2 = unit(v);
-  const V3<double> e3 = cross(e1, e2);
+  const V3<R> e2 = unit(v);
+  const V3<R> e3 = cross(e1, e2);
   Q[0] = e1.x; Q[1] = e2.x; Q[2] = e3.x;
   Q[3] = e1.y; Q[4] = e2.y; Q[5] = e3.y;
   Q[6] = e1.z; Q[7] = e2.z; Q[8] = e3.z;
 }
 
+template <class R>
 struct CanonicalResidue {
-  V3<double> N, CA, C, CB;
-  double Q0[9];  // frame of the canonical residue
+  V3<R> N, CA, C, CB;
+  R Q0[9];  // frame of the canonical residue
 };
 
-__device__ __forceinline__ CanonicalResidue canonical_residue(const Geom<double>& g) {
-  CanonicalResidue r;
+template <class R>
+__device__ __forceinline__ CanonicalResidue<R> canonical_residue(const Geom<R>& g) {
+  CanonicalResidue<R> r;
   first_residue(g, r.N, r.CA, r.C);
   r.CB = cbeta(g, r.N, r.CA, r.C);
   residue_frame(r.N, r.CA, r.C, r.Q0);
@@ -246,14 +289,14 @@ __device__ __forceinline__ CanonicalResidue canonical_residue(const Geom<double>
 }
 
 // T_i: canonical residue -> residue i in the frame of canonical residue i-1.
-__device__ __forceinline__ Aff<double> residue_step(const Geom<double>& g,
-                                                    const CanonicalResidue& r, double psi,
-                                                    double phi) {
-  V3<double> N = r.N, CA = r.CA, C = r.C;
+template <class R>
+__device__ __forceinline__ Aff<R> residue_step(const Geom<R>& g, const CanonicalResidue<R>& r,
+                                               R psi, R phi) {
+  V3<R> N = r.N, CA = r.CA, C = r.C;
   next_residue(g, N, CA, C, psi, phi);
-  double Q1[9];
+  R Q1[9];
   residue_frame(N, CA, C, Q1);
-  Aff<double> T;
+  Aff<R> T;
   // M = Q1 Q0^T, t = CA1 - M CA0
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -292,7 +335,7 @@ __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH t
   const int lane = r % width;
   const int wpc = tpc / width;  // warps per chain
   const int wi = r / width;     // this thread's warp within its chain
-  const CanonicalResidue cr = canonical_residue(g);
+  const CanonicalResidue<double> cr = canonical_residue(g);
   const int nb = (L + tpc - 1) / tpc;
   const int r0 = min(L, r * nb), r1 = min(L, r0 + nb);
   Aff<double> agg = identity_map<double>();

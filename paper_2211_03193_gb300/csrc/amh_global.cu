@@ -18,7 +18,7 @@ namespace amh {
 
 namespace {
 
-constexpr int kFC = 16;  // fixed-side atoms per work item
+constexpr int kFC = 32;  // fixed-side atoms per work item
 
 template <class R>
 struct AccT {
@@ -29,21 +29,22 @@ struct AccT<double> {
   using T = double;
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+// Regions are 32-byte aligned so 4-wide points of either precision load
+// with vector instructions.
+__host__ __device__ inline size_t align16(size_t x) { return (x + 31) & ~size_t(31); }
+
 
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cbx, cby, cbz, maps, part, ecur, thn, lnu, acc, commit, flag, scan, bars,
+  size_t theta, bb, cb, maps, part, ecur, thn, lnu, acc, commit, flag, scan, bars,
       ring, total;
   // D ring slots per warp of 32/C rows of RB bytes (D = 0: no staging)
   __host__ __device__ Layout(int Lmax, int nmax, int W, int D = 0, int RB = 0) {
     size_t o = 0;
     theta = o; o = align16(o + sizeof(R) * (size_t)nmax * C);
     bb = o;    o = align16(o + sizeof(R) * (size_t)Lmax * 9 * C);
-    cbx = o;   o = align16(o + sizeof(R) * (size_t)Lmax * C);
-    cby = o;   o = align16(o + sizeof(R) * (size_t)Lmax * C);
-    cbz = o;   o = align16(o + sizeof(R) * (size_t)Lmax * C);
+    cb = o;    o = align16(o + sizeof(Pt4<R>) * (size_t)Lmax * C);
     maps = o;  o = align16(o + sizeof(R) * 36 * C);
     part = o;  o = align16(o + sizeof(double) * 3 * (size_t)W * C);
     ecur = o;  o = align16(o + sizeof(double) * C);
@@ -64,9 +65,7 @@ template <class R, int C>
 struct Shm {
   R* theta;  // [k][C]
   R* bb;     // [((i*3+atom)*3+xyz)][C], atom 0 N, 1 CA, 2 C
-  R* cbx;    // [i][C]
-  R* cby;
-  R* cbz;
+  Pt4<R>* cb4;  // [i][C]
   R* maps;   // [C][36]: A1, A2, A21
   double* part;  // [W][C][3]
   double* ecur;  // [C]
@@ -81,9 +80,7 @@ struct Shm {
   __device__ Shm(unsigned char* base, const Layout<R, C>& l) {
     theta = (R*)(base + l.theta);
     bb = (R*)(base + l.bb);
-    cbx = (R*)(base + l.cbx);
-    cby = (R*)(base + l.cby);
-    cbz = (R*)(base + l.cbz);
+    cb4 = (Pt4<R>*)(base + l.cb);
     maps = (R*)(base + l.maps);
     part = (double*)(base + l.part);
     ecur = (double*)(base + l.ecur);
@@ -97,7 +94,16 @@ struct Shm {
     ring = base + l.ring;
   }
   __device__ V3<R> cb(int i, int c) const {
-    return v3<R>(cbx[i * C + c], cby[i * C + c], cbz[i * C + c]);
+    const Pt4<R> p = cb4[i * C + c];
+    return v3<R>(p.x, p.y, p.z);
+  }
+  __device__ void set_cb(int i, int c, V3<R> v) {
+    Pt4<R> p;
+    p.x = v.x;
+    p.y = v.y;
+    p.z = v.z;
+    p.w = (R)0;
+    cb4[i * C + c] = p;
   }
   __device__ V3<R> atom(int i, int a, int c) const {
     const R* p = bb + (size_t)((i * 3 + a) * 3) * C + c;
@@ -128,9 +134,7 @@ __device__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
         s.set_atom(i, 0, c, to_r<R>(N));
         s.set_atom(i, 1, c, to_r<R>(CA));
         s.set_atom(i, 2, c, to_r<R>(Cc));
-        s.cbx[i * C + c] = (R)CB.x;
-        s.cby[i * C + c] = (R)CB.y;
-        s.cbz[i * C + c] = (R)CB.z;
+        s.set_cb(i, c, to_r<R>(CB));
       },
       s.scan);
 }
@@ -194,12 +198,15 @@ __device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P)
   full_energy(s, a.tab, P.tab_off, P.L);
 }
 
+// A map is 12 values at a 4-value boundary of the maps region: three
+// vector loads.
 template <class R, int C>
 __device__ __forceinline__ void load_aff(const R* src, Aff<R>& A) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) A.m[i] = src[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) A.t[i] = src[9 + i];
+  const Pt4<R>* q = reinterpret_cast<const Pt4<R>*>(src);
+  const Pt4<R> a = q[0], b = q[1], d = q[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.t[0] = d.y; A.t[1] = d.z; A.t[2] = d.w;
 }
 
 template <class R>
@@ -252,19 +259,19 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
       const V3<R> xf = s.cb(f, c);
       R e0, e1, e2 = 0, e21 = 0;
       if constexpr (TEX) {
-        e0 = pair_term_tex(rowe, dist_(xf, xm), tb);
-        e1 = pair_term_tex(rowe, dist_(xf, y1), tb);
+        e0 = pair_term_tex(rowe, dist_fast(xf, xm), tb);
+        e1 = pair_term_tex(rowe, dist_fast(xf, y1), tb);
         if (FUSED) {
-          e2 = pair_term_tex(rowe, dist_(xf, y2), tb);
-          e21 = pair_term_tex(rowe, dist_(xf, y21), tb);
+          e2 = pair_term_tex(rowe, dist_fast(xf, y2), tb);
+          e21 = pair_term_tex(rowe, dist_fast(xf, y21), tb);
         }
         rowe += step * tb.Bp;
       } else {
-        e0 = pair_term(row, dist_(xf, xm), tb);
-        e1 = pair_term(row, dist_(xf, y1), tb);
+        e0 = pair_term(row, dist_fast(xf, xm), tb);
+        e1 = pair_term(row, dist_fast(xf, y1), tb);
         if (FUSED) {
-          e2 = pair_term(row, dist_(xf, y2), tb);
-          e21 = pair_term(row, dist_(xf, y21), tb);
+          e2 = pair_term(row, dist_fast(xf, y2), tb);
+          e21 = pair_term(row, dist_fast(xf, y21), tb);
         }
         row += (long long)step * tb.Bp;
       }
@@ -435,10 +442,7 @@ __device__ void commit_moves(Shm<R, C>& s, int m0, int m1) {
     if (atom < 3) {
       s.set_atom(i, atom, c, apply(A, s.atom(i, atom, c)));
     } else {
-      V3<R> y = apply(A, s.cb(i, c));
-      s.cbx[i * C + c] = y.x;
-      s.cby[i * C + c] = y.y;
-      s.cbz[i * C + c] = y.z;
+      s.set_cb(i, c, apply(A, s.cb(i, c)));
     }
   }
 }

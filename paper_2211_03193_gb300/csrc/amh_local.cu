@@ -8,9 +8,16 @@
 // torsions between its residues, T(W) = [2(c-h)+1, 2(c+h)]; moves whose
 // torsion index differs by a multiple of 4h have disjoint T(W), so one
 // colour (all k with the same k mod 4h) is evaluated concurrently, one
-// thread per window, from window-local coordinates built by NeRF in a
-// frame of the window's own first residue (rigid motion leaves V_local
-// unchanged).  Colours run in ascending order, k ascending within a colour.
+// thread per window, from window-local coordinates in the frame of the
+// window's own first residue (rigid motion leaves V_local unchanged).
+// Colours run in ascending order, k ascending within a colour.
+//
+// Window coordinates come from residue transforms: with ideal geometry
+// residue i sits at T_{lo+1} o ... o T_i applied to a canonical residue in
+// the frame of residue lo, and T_i depends on (psi_{i-1}, phi_i) only.  The
+// CTA keeps every T_i of its chains in shared memory and recomputes T_p(k)
+// when move k is accepted; T_p(k) belongs to the window of move k alone
+// within a colour.
 #include "amh_internal.h"
 
 namespace amh {
@@ -26,17 +33,19 @@ struct AccT<double> {
   using T = double;
 };
 
-__host__ __device__ inline size_t align16l(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t align32l(size_t x) { return (x + 31) & ~size_t(31); }
 
 template <class R>
 struct LLayout {
-  size_t theta, cbs, acc, total;
+  size_t theta, tr, cbs, acc, total;
   __host__ __device__ LLayout(int nmax, int Gc, int threads, int window) {
     const int h = window / 2;
+    const int Lmax = nmax / 2;
     size_t o = 0;
-    theta = o; o = align16l(o + sizeof(R) * (size_t)nmax * Gc);
-    cbs = o;   o = align16l(o + sizeof(R) * (size_t)(2 * h + 1) * 3 * threads);
-    acc = o;   o = align16l(o + sizeof(unsigned long long) * Gc);
+    theta = o; o = align32l(o + sizeof(R) * (size_t)nmax * Gc);
+    tr = o;    o = align32l(o + sizeof(Pt4<R>) * 3 * (size_t)Lmax * Gc);
+    cbs = o;   o = align32l(o + sizeof(R) * (size_t)(2 * h + 1) * 3 * threads);
+    acc = o;   o = align32l(o + sizeof(unsigned long long) * Gc);
     total = o;
   }
 };
@@ -46,17 +55,34 @@ __device__ __forceinline__ int colour_count(int n, int ncol, int r) {
   return r < n ? (n - 1 - r) / ncol + 1 : 0;
 }
 
+// Pair term through the texture path (FP32) or the table rows (FP64).
+template <class R>
+__device__ __forceinline__ R local_term(const Tab<R>& tb, long long tab_off, int row, R d);
+template <>
+__device__ __forceinline__ float local_term<float>(const Tab<float>& tb, long long tab_off,
+                                                   int row, float d) {
+  if (tb.tex) return pair_term_tex((int)tab_off + row * tb.Bp, d, tb);
+  return pair_term(tb.E + tab_off + (long long)row * tb.Bp, d, tb);
+}
+template <>
+__device__ __forceinline__ double local_term<double>(const Tab<double>& tb, long long tab_off,
+                                                     int row, double d) {
+  return pair_term(tb.E + tab_off + (long long)row * tb.Bp, d, tb);
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(32) unsigned char smem[];
   __shared__ int s_group;
   const LLayout<R> lay(a.nmax, Gc, blockDim.x, a.window);
   R* th_s = (R*)(smem + lay.theta);          // [k][Gc]
+  Pt4<R>* tr_s = (Pt4<R>*)(smem + lay.tr);   // [i][Gc][3]: T_i, i >= 1
   R* cbs = (R*)(smem + lay.cbs);             // [(j*3+xyz)][threads]
   unsigned long long* acc_s = (unsigned long long*)(smem + lay.acc);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int h = a.window / 2;
   const int ncol = 4 * h > 1 ? 4 * h : 1;
+  const CanonicalResidue<R> cr = canonical_residue(a.geom);
   for (;;) {
     __syncthreads();
     if (tid == 0) s_group = atomicAdd(a.queue, 1);
@@ -73,6 +99,12 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
       th_s[k * Gc + c] = v;
     }
     if (tid < Gc) acc_s[tid] = 0ull;
+    __syncthreads();
+    for (int idx = tid; idx < (L - 1) * Gc; idx += nt) {
+      const int i = 1 + idx / Gc, c = idx % Gc;
+      aff_store4(tr_s + ((size_t)i * Gc + c) * 3,
+                 residue_step(a.geom, cr, th_s[(2 * i - 1) * Gc + c], th_s[2 * i * Gc + c]));
+    }
     const long long t0 = a.tcount[G.chain0];
     const long long nsw = a.steps_are_sweeps ? a.steps : a.steps / n;
     __syncthreads();
@@ -97,45 +129,44 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
           const int p = (k + 1) >> 1;
           double dE = 0.0;
           if (p > lo && p <= hi) {
-            // window-local G(s) of residues lo..hi; remember the bond axis
-            V3<R> N, CA, Cc, Pax, Qax;
-            first_residue(a.geom, N, CA, Cc);
-            Pax = N;
-            Qax = CA;
-            for (int rr = lo;; ++rr) {
-              const V3<R> cb = cbeta<R, true>(a.geom, N, CA, Cc);
+            // window coordinates: residue rr at M = T_{lo+1} o ... o T_rr
+            // applied to the canonical residue; remember the bond axis
+            Aff<R> M = identity_map<R>();
+            V3<R> Pax = cr.N, Qax = cr.CA;
+            for (int rr = lo; rr <= hi; ++rr) {
+              if (rr > lo) M = compose(M, aff_load4(tr_s + ((size_t)rr * Gc + c) * 3));
+              const V3<R> cb = apply(M, cr.CB);
               const int j = rr - lo;
               cbs[(j * 3 + 0) * nt + tid] = cb.x;
               cbs[(j * 3 + 1) * nt + tid] = cb.y;
               cbs[(j * 3 + 2) * nt + tid] = cb.z;
               if (rr == i) {
                 if (k & 1) {  // psi_i: CA_i -> C_i
-                  Pax = CA;
-                  Qax = Cc;
+                  Pax = apply(M, cr.CA);
+                  Qax = apply(M, cr.C);
                 } else {      // phi_i: N_i -> CA_i
-                  Pax = N;
-                  Qax = CA;
+                  Pax = apply(M, cr.N);
+                  Qax = apply(M, cr.CA);
                 }
               }
-              if (rr == hi) break;
-              next_residue<R, true>(a.geom, N, CA, Cc, th_s[(2 * rr + 1) * Gc + c],
-                                    th_s[(2 * rr + 2) * Gc + c]);
             }
             const Aff<R> A = rotation(Pax, Qax, wrap_angle(thn - th));
             typename AccT<R>::T acc = 0;
-            const auto* tab = a.tab.E + P.tab_off;
             for (int b = p; b <= hi; ++b) {
               const int jb = b - lo;
               const V3<R> xb = v3<R>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
                                      cbs[(jb * 3 + 2) * nt + tid]);
               const V3<R> yb = apply(A, xb);
+              // rows (aa, b), aa ascending: r(aa+1, b) - r(aa, b) = L - aa - 2
+              int row = row_of(L, lo, b);
               for (int aa = lo; aa < p; ++aa) {
                 const int ja = aa - lo;
                 const V3<R> xa = v3<R>(cbs[(ja * 3 + 0) * nt + tid],
                                        cbs[(ja * 3 + 1) * nt + tid],
                                        cbs[(ja * 3 + 2) * nt + tid]);
-                const auto* row = tab + (long long)row_of(L, aa, b) * a.tab.Bp;
-                acc += pair_term(row, dist_(xa, yb), a.tab) - pair_term(row, dist_(xa, xb), a.tab);
+                acc += local_term(a.tab, P.tab_off, row, dist_fast(xa, yb)) -
+                       local_term(a.tab, P.tab_off, row, dist_fast(xa, xb));
+                row += L - aa - 2;
               }
             }
             dE = (double)acc;
@@ -145,6 +176,11 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
           if (accept) {
             th_s[k * Gc + c] = thn;
             atomicAdd(&acc_s[c], 1ull);
+            // T_p depends on torsions 2p-1 and 2p, one of which is k
+            if (p >= 1 && p < L)
+              aff_store4(tr_s + ((size_t)p * Gc + c) * 3,
+                         residue_step(a.geom, cr, th_s[(2 * p - 1) * Gc + c],
+                                      th_s[2 * p * Gc + c]));
           }
           const long long v = t0 + sw * n + slot0 + w;
           if (chain < a.trace_chains && v < a.trace_cap) {

@@ -4,10 +4,15 @@
 
 namespace amh {
 
-// Shared memory of one gradient CTA (256 threads): coordinates and forces in
-// R, suffix sums in FP64, and the chain-building scan's warp totals.
+// Shared memory of one gradient CTA (256 threads): coordinates and partial
+// forces in R, suffix sums in FP64, and the chain-building scan's warp
+// totals.
+// Parts of the a range per pair-force item (partial forces kept apart so
+// the sum needs no atomics and its order is fixed).
+constexpr int kGradParts = 4;
+
 size_t grad_smem_bytes(size_t rsize, int L) {
-  return ((rsize * 18 * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1) +
+  return ((rsize * (12 + 3 * kGradParts) * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1) +
          sizeof(double) * 12 * 8;
 }
 
@@ -90,8 +95,9 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = 2 * L;
   R* X = (R*)smem;          // [4][L][3]: N, CA, C, CB
-  R* gb = X + 12 * L;       // [2][L][3] partial dV/dx_b (two halves of the a range)
-  double* GM = (double*)(smem + (((size_t)sizeof(R) * 18 * L + 15) & ~(size_t)15));  // [L+1][6]
+  R* gb = X + 12 * L;       // [kGradParts][L][3] partial dV/dx_b (parts of the a range)
+  double* GM = (double*)(smem + (((size_t)sizeof(R) * (12 + 3 * kGradParts) * L + 15) &
+                                 ~(size_t)15));  // [L+1][6]
   double* scan = GM + (size_t)6 * (L + 1);  // [8][12] warp totals of the chain-building scan
   double* cache = scan + 8 * 12;            // [L][12] residue transforms (if use_cache)
   __shared__ double wpart[64];  // warp energy partials, then the suffix scan's 8 x 6 totals
@@ -112,32 +118,44 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
       scan, use_cache ? cache : nullptr);
   __syncthreads();
   const R* CB = X + 9 * L;
-  // pair forces: item (b, half) sums over a in half of [0, L); each pair is
-  // visited from both ends, so no atomics are needed
+  // pair forces: item (b, q) sums over a in part q of [0, L); each pair is
+  // visited from both ends, so no atomics are needed.  Rows advance
+  // incrementally: r(a+1, b) - r(a, b) = L - a - 2 below b, +1 above it.
   double esum = 0.0;
-  const int half = (L + 1) / 2;
-  for (int it = tid; it < 2 * L; it += nt) {
-    const int b = it >> 1, h = it & 1;
-    const int a0 = h ? half : 0, a1 = h ? L : half;
+  const int chunk = (L + kGradParts - 1) / kGradParts;
+  for (int it = tid; it < kGradParts * L; it += nt) {
+    const int b = it / kGradParts, q = it - b * kGradParts;
+    const int a0 = min(L, q * chunk), a1 = min(L, a0 + chunk);
     const V3<R> xb = v3<R>(CB[3 * b], CB[3 * b + 1], CB[3 * b + 2]);
     R gx = 0, gy = 0, gz = 0;
     R epart = 0;
-    for (int a = a0; a < a1; ++a) {
-      if (a == b) continue;
-      const V3<R> xa = v3<R>(CB[3 * a], CB[3 * a + 1], CB[3 * a + 2]);
-      const int ra = min(a, b), rb = max(a, b);
-      const auto* row = tb.E + tab_off + (long long)row_of(L, ra, rb) * tb.Bp;
-      const V3<R> dlt = xb - xa;
-      const R d = sqrt(dot(dlt, dlt));
+    // dV/dx_b from pair (a, b): e'(d) (x_b - x_a) / d, 1/d from one rsqrt
+    auto pair = [&](int a, const typename Vec2<R>::T* row) -> R {
+      const V3<R> dlt = xb - v3<R>(CB[3 * a], CB[3 * a + 1], CB[3 * a + 2]);
+      const R d2 = fma(dlt.z, dlt.z, fma(dlt.y, dlt.y, fma(dlt.x, dlt.x, R(1e-30))));
+      const R inv = rsqrt_(d2);
       R sl;
-      const R e = pair_term_slope(row, d, tb, &sl);
-      const R f = d > R(0) ? sl / d : R(0);
+      const R e = pair_term_slope(row, d2 * inv, tb, &sl);
+      const R f = sl * inv;
       gx += f * dlt.x;
       gy += f * dlt.y;
       gz += f * dlt.z;
-      if (a < b) epart += e;
+      return e;
+    };
+    const int e1 = min(a1, b);
+    if (a0 < e1) {
+      const auto* row = tb.E + tab_off + (long long)row_of(L, a0, b) * tb.Bp;
+      for (int a = a0; a < e1; ++a) {
+        epart += pair(a, row);
+        row += (long long)(L - a - 2) * tb.Bp;
+      }
     }
-    R* gp = gb + ((size_t)h * L + b) * 3;
+    const int s2 = max(a0, b + 1);
+    if (s2 < a1) {
+      const auto* row = tb.E + tab_off + (long long)row_of(L, b, s2) * tb.Bp;
+      for (int a = s2; a < a1; ++a, row += tb.Bp) pair(a, row);
+    }
+    R* gp = gb + ((size_t)q * L + b) * 3;
     gp[0] = gx;
     gp[1] = gy;
     gp[2] = gz;
@@ -146,8 +164,13 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
   for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
   if ((tid & 31) == 0) wpart[tid >> 5] = esum;
   __syncthreads();
-  // fold the two halves: g_b in the first half of gb
-  for (int q = tid; q < 3 * L; q += nt) gb[q] += gb[3 * L + q];
+  // fold the parts in order: g_b in part 0 of gb
+  for (int q = tid; q < 3 * L; q += nt) {
+    R g = gb[q];
+#pragma unroll
+    for (int h = 1; h < kGradParts; ++h) g += gb[(size_t)h * 3 * L + q];
+    gb[q] = g;
+  }
   if (tid == 0) {
     double e = 0.0;
     for (int w = 0; w < (nt >> 5); ++w) e += wpart[w];
