@@ -319,17 +319,18 @@ __device__ __forceinline__ Aff<double> shfl_up_aff(const Aff<double>& A, int off
   return B;
 }
 
-// Build G(s) of `nch` chains with all threads of the CTA: chain c uses the
-// tpc = blockDim.x / nslots consecutive threads starting at c * tpc (tpc a
-// power of two).  theta(c, k) reads torsion k of chain c; emit(c, i, N, CA,
-// C, CB) stores residue i.  scratch: nslots * max(tpc/32, 1) * 12 doubles of
-// shared memory.  cache (optional, nslots * L * 12 doubles of shared memory)
-// keeps each T_i so the second pass does not recompute it.  Must be called
-// by every thread of the CTA.
+// Build G(s) of `nch` chains with the first nthreads threads of the CTA
+// (0: all): chain c uses the tpc = nthreads / nslots consecutive threads
+// starting at c * tpc (tpc a power of two).  theta(c, k) reads torsion k of
+// chain c; emit(c, i, N, CA, C, CB) stores residue i.  scratch: nslots *
+// max(tpc/32, 1) * 12 doubles of shared memory.  cache (optional, nslots * L
+// * 12 doubles of shared memory) keeps each T_i so the second pass does not
+// recompute it.  Must be called by every one of those threads; with tpc > 32
+// it synchronises the whole CTA, so then nthreads must be the CTA.
 template <class TH, class EMIT>
 __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH theta, EMIT emit,
-                                  double* scratch, double* cache = nullptr) {
-  const int tpc = blockDim.x / nslots;
+                                  double* scratch, double* cache = nullptr, int nthreads = 0) {
+  const int tpc = (nthreads ? nthreads : (int)blockDim.x) / nslots;
   const int c = threadIdx.x / tpc, r = threadIdx.x % tpc;
   const int width = tpc < 32 ? tpc : 32;
   const int lane = r % width;

@@ -587,7 +587,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       if (threadIdx.x < C) {
         const int c = threadIdx.x;
         const int chain = G.chain0 + c;
-        const int acc = (double)s.lnu[c] < -0.0 / chain_T(a, P, chain);
+        const int acc = (double)s.lnu[c] * chain_T(a, P, chain) < -0.0;
         if (acc) s.theta[k * C + c] = s.thn[c];
         s.acc[c] += acc;
         put_trace(a, c < G.nchains, chain, t, k, acc, s.thn[c], s.lnu[c], 0.0);
@@ -636,7 +636,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         d21 += pp[2];
       }
       const double Tc = chain_T(a, P, chain);
-      const int acc1 = (double)s.lnu[c] < -d1 / Tc;
+      // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE (no division)
+      const int acc1 = (double)s.lnu[c] * Tc < -d1;
       int code = acc1;
       double dE = acc1 ? d1 : 0.0;
       if (acc1) s.theta[k * C + c] = s.thn[c];
@@ -644,7 +645,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       int acc2 = 0;
       if (fused) {
         const double e2 = acc1 ? d21 : d2;
-        acc2 = (double)s.lnu[C + c] < -e2 / Tc;
+        acc2 = (double)s.lnu[C + c] * Tc < -e2;
         if (acc2) {
           code = acc1 ? 3 : 2;
           dE += e2;

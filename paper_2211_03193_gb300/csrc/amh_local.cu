@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
             dE = (double)acc;
           }
           const double Tc = a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
-          const int accept = (double)lnu < -dE / Tc;
+          const int accept = (double)lnu * Tc < -dE;  // ln u < -dE / T, T > 0
           if (accept) {
             th_s[k * Gc + c] = thn;
             atomicAdd(&acc_s[c], 1ull);

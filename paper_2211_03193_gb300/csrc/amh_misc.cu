@@ -103,19 +103,21 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
   __shared__ double wpart[64];  // warp energy partials, then the suffix scan's 8 x 6 totals
   const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const R* th = theta + (size_t)v * n;
-  // G(s) built in FP64 by all threads, stored in R (as the sweeps' resync)
-  build_chains_scan(
-      geom, L, 1, [&](int, int k) { return (double)th[k]; },
-      [&](int, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
-        const V3<double> at[4] = {N, CA, Cc, CB};
+  // G(s) built in FP64 by one warp (FP64 is the scarce pipe: a wider scan
+  // composes more transforms in all), stored in R as the sweeps' resync does
+  if (tid < 32)
+    build_chains_scan(
+        geom, L, 1, [&](int, int k) { return (double)th[k]; },
+        [&](int, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
+          const V3<double> at[4] = {N, CA, Cc, CB};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          X[(q * L + i) * 3 + 0] = (R)at[q].x;
-          X[(q * L + i) * 3 + 1] = (R)at[q].y;
-          X[(q * L + i) * 3 + 2] = (R)at[q].z;
-        }
-      },
-      scan, use_cache ? cache : nullptr);
+          for (int q = 0; q < 4; ++q) {
+            X[(q * L + i) * 3 + 0] = (R)at[q].x;
+            X[(q * L + i) * 3 + 1] = (R)at[q].y;
+            X[(q * L + i) * 3 + 2] = (R)at[q].z;
+          }
+        },
+        scan, use_cache ? cache : nullptr, 32);
   __syncthreads();
   const R* CB = X + 9 * L;
   // pair forces: item (b, q) sums over a in part q of [0, L); each pair is
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
     const int e1 = min(a1, b);
     if (a0 < e1) {
       const auto* row = tb.E + tab_off + (long long)row_of(L, a0, b) * tb.Bp;
+#pragma unroll 4
       for (int a = a0; a < e1; ++a) {
         epart += pair(a, row);
         row += (long long)(L - a - 2) * tb.Bp;
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
     const int s2 = max(a0, b + 1);
     if (s2 < a1) {
       const auto* row = tb.E + tab_off + (long long)row_of(L, b, s2) * tb.Bp;
+#pragma unroll 4
       for (int a = s2; a < a1; ++a, row += tb.Bp) pair(a, row);
     }
     R* gp = gb + ((size_t)q * L + b) * 3;
