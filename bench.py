@@ -454,6 +454,9 @@ def run_ours(args):
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
                    stage_table=args.stage, table_texture=args.texture)
     C, thr, D = samp.launch_config()
+    # device table: one 8-byte entry per bin, rows padded to an even bin count
+    B = len(synth.edges_by_name(w["bins"])) - 1
+    tab_mb = (L * (L - 1) // 2) * ((B + 1) & ~1) * (8 if w["precision"] == 32 else 16) / 1e6
     sched = schedule_for(w, seed=1 + rank)
     cyc = w["cycle"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -574,7 +577,8 @@ def run_ours(args):
            "config": {"workload": args.workload, "L": L, "chains_per_gpu": chains, "bins": w["bins"], "schedule": "10 local (d=8) : 1 global per step, "
                       "T 2.0->0.05, sigma 10->4 deg over %d sweeps" % w["total_sweeps"],
                       "proposals_per_step_per_gpu": props_step, "l2": "flushed between steps "
-                      "(256 MB write); table 6.6 MB is L2-resident within a step",
+                      "(256 MB write); the %.1f MB table is L2-resident within a step" % (
+                          tab_mb,),
                       "chains_per_cta": C, "threads_per_cta": thr, "stage_depth": D,
                       "parallelism": "independent chains per GPU (replicas)"},
            "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),

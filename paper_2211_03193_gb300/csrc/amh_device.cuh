@@ -401,9 +401,14 @@ __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH t
 
 // ------------------------------------------------------------------ table
 // Pair term of Eq. 5: -ln p interpolated linearly between evenly spaced bin
-// centres c_j = c0 + j w, flat outside [c_0, c_{B-1}].  Each row stores, per
-// bin, the pair (E_j, E_{j+1} - E_j) so one 8-byte load and one FMA give the
-// term; the last bin and the padding hold (E_{B-1}, 0).
+// centres c_j = c0 + j w, flat outside [c_0, c_{B-1}].  Each row holds one
+// 8-byte entry per bin, so one load and one FMA give the term:
+//  FP64: (E_j, E_{j+1} - E_j), term = E_j + (u - j) (E_{j+1} - E_j) with u the
+//        bin coordinate (d - c0)/w clamped to [0, B-1];
+//  FP32: (E_j - j D_j, (B-1) D_j), D_j = E_{j+1} - E_j, term = fmaf(us, .y,
+//        .x) with us = u / (B-1) in [0, 1]: the same line, with j folded into
+//        the entry so the term needs no fractional part.
+// The last bin and the padding hold (E_{B-1}, 0).
 template <class R>
 struct Vec2;
 template <>
@@ -457,7 +462,6 @@ __device__ __forceinline__ float pair_term(const float2* __restrict__ row, float
                                            const Tab<float>& tb) {
   const float us = __saturatef(fmaf(d, tb.k1, tb.k2));
   const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
-  const float t = fmaf(us, tb.umax, 8388608.0f - f);
   const char* base = reinterpret_cast<const char*>(row) - 8ull * 0x4B000000u;
   float2 v;
   // one wide multiply-add forms the entry address from the float's bits
@@ -465,20 +469,28 @@ __device__ __forceinline__ float pair_term(const float2* __restrict__ row, float
       "ld.global.nc.v2.f32 {%0, %1}, [ad];\n\t}"
       : "=f"(v.x), "=f"(v.y)
       : "r"((unsigned)__float_as_int(f)), "l"(base));
-  return fmaf(t, v.y, v.x);
+  return fmaf(us, v.y, v.x);
 }
 
 // Value and slope d e / d d (zero on the flat ends).
-template <class R>
-__device__ __forceinline__ R pair_term_slope(const typename Vec2<R>::T* __restrict__ row, R d,
-                                             const Tab<R>& tb, R* slope) {
-  const R u0 = fma(d, tb.inv_w, tb.off);
-  const R u = fmin(fmax(u0, R(0)), tb.umax);
-  R jf;
+__device__ __forceinline__ double pair_term_slope(const double2* __restrict__ row, double d,
+                                                  const Tab<double>& tb, double* slope) {
+  const double u0 = fma(d, tb.inv_w, tb.off);
+  const double u = fmin(fmax(u0, 0.0), tb.umax);
+  double jf;
   const int j = floor_small(u, &jf);
-  const typename Vec2<R>::T v = __ldg(row + j);
-  *slope = (u0 >= R(0) && u0 < tb.umax) ? v.y * tb.inv_w : R(0);
+  const double2 v = __ldg(row + j);
+  *slope = (u0 >= 0.0 && u0 < tb.umax) ? v.y * tb.inv_w : 0.0;
   return fma(u - jf, v.y, v.x);
+}
+__device__ __forceinline__ float pair_term_slope(const float2* __restrict__ row, float d,
+                                                 const Tab<float>& tb, float* slope) {
+  const float s0 = fmaf(d, tb.k1, tb.k2);
+  const float us = __saturatef(s0);
+  const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
+  const float2 v = __ldg(row + (__float_as_int(f) - 0x4B000000));
+  *slope = (s0 >= 0.f && s0 < 1.f) ? v.y * tb.k1 : 0.f;
+  return fmaf(us, v.y, v.x);
 }
 
 // The same term fetched through the texture path from a 32-bit entry index
@@ -487,9 +499,8 @@ __device__ __forceinline__ R pair_term_slope(const typename Vec2<R>::T* __restri
 __device__ __forceinline__ float pair_term_tex(int row_e, float d, const Tab<float>& tb) {
   const float us = __saturatef(fmaf(d, tb.k1, tb.k2));
   const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
-  const float t = fmaf(us, tb.umax, 8388608.0f - f);
   const float2 v = tex1Dfetch<float2>(tb.tex, row_e - 0x4B000000 + __float_as_int(f));
-  return fmaf(t, v.y, v.x);
+  return fmaf(us, v.y, v.x);
 }
 
 // The same term read from a row staged in shared memory (32-bit address:
@@ -497,11 +508,10 @@ __device__ __forceinline__ float pair_term_tex(int row_e, float d, const Tab<flo
 __device__ __forceinline__ float pair_term_smem(uint32_t row, float d, const Tab<float>& tb) {
   const float us = __saturatef(fmaf(d, tb.k1, tb.k2));
   const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
-  const float t = fmaf(us, tb.umax, 8388608.0f - f);
   const uint32_t ad = row - 8u * 0x4B000000u + 8u * (uint32_t)__float_as_int(f);
   float2 v;
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(ad));
-  return fmaf(t, v.y, v.x);
+  return fmaf(us, v.y, v.x);
 }
 
 // ------------------------------------------------------------------ async copies

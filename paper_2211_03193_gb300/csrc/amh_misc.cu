@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
 }
 
 // ---------------------------------------------------------------- table
-// Entry j of a row: (E_j, E_{j+1} - E_j) with E = -ln max(p, 1e-300); the
+// Entry j of a row, E = -ln max(p, 1e-300) and D_j = E_{j+1} - E_j: (E_j,
+// D_j) in FP64, (E_j - j D_j, (B-1) D_j) in FP32 (the layouts of Tab); the
 // last bin and the padding hold (E_{B-1}, 0).
 __device__ __forceinline__ double neglog_p(double q, int neglog) {
   return neglog ? q : -log(q > 1e-300 ? q : 1e-300);
@@ -225,8 +226,14 @@ __global__ void prep_table_kernel(const double* __restrict__ p, long long rows, 
     const double e0 = neglog_p(pr[j < B ? j : B - 1], neglog);
     const double e1 = j + 1 < B ? neglog_p(pr[j + 1], neglog) : e0;
     typename Vec2<R>::T v;
-    v.x = (R)e0;
-    v.y = (R)(e1 - e0);
+    if (sizeof(R) == 8) {  // (E_j, D_j)
+      v.x = (R)e0;
+      v.y = (R)(e1 - e0);
+    } else {               // (E_j - j D_j, (B-1) D_j): see Tab
+      const double D = e1 - e0;
+      v.x = (R)(e0 - (double)j * D);
+      v.y = (R)((double)(B - 1) * D);
+    }
     out[i] = v;
   }
 }
