@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target measurement")
-    ap.add_argument("--experiment", default="", choices=["", "schemes", "forms", "batched"],
+    ap.add_argument("--experiment", default="", choices=["", "schemes", "forms", "batched", "grad"],
                     help="schemes: AMH vs plain MH vs MH with noisy restarts (L=150); forms: "
                          "batched FP32 vs one-chain FP64 (L=300); batched: 64 uneven proteins")
     ap.add_argument("--chains-per-cta", type=int, default=0,
@@ -209,11 +209,37 @@ def cpu_baseline(w, seed, budget_s=12.0):
         if time.perf_counter() - t0 > budget_s and s % w["cycle"] == 0:
             break
     dt = time.perf_counter() - t0
+    # one core: one chain through one cycle of the same schedule
+    s1 = S[0].copy()
+    t1 = time.perf_counter()
+    for q in range(w["cycle"]):
+        mode, T, sigma = sched.params(q)
+        s1, _, _ = P.run(s1, mode, w["window"], T, sigma, q * n, n, seed, 0)
+    dt1 = time.perf_counter() - t1
     return {"value": props / dt, "unit": "proposals/s", "cores": cores, "kind": "oracle",
             "sample": "%d chains x %d sweeps (%d cycles of %d local + %d global, L=%d) of the "
                       "same schedule, FP64, OpenMP over chains" % (
                           cores, s, s // w["cycle"], w["n_local"], w["n_global"], w["L"]),
-            "seconds": dt}
+            "seconds": dt, "single_core_value": w["cycle"] * n / dt1,
+            "single_core_sample": "1 chain x 1 cycle (%d sweeps)" % w["cycle"]}
+
+
+def measured_peaks():
+    """FP32 FMA, MUFU square-root and L2 read rates of this GPU, from the
+    microbenchmarks in libamh_peaks.so (or None if it cannot run)."""
+    import ctypes
+    from paper_2211_03193_gb300 import build
+    try:
+        lib = ctypes.CDLL(build.PEAKS_LIB)
+        f, m, l2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        if lib.amh_measure_peaks(ctypes.byref(f), ctypes.byref(m), ctypes.byref(l2)) != 0:
+            return None
+    except OSError:
+        return None
+    return {"fp32_tflops": 2 * f.value / 1e12, "mufu_sqrt_per_s": m.value,
+            "l2_read_gbs": l2.value / 1e9,
+            "how": "libamh_peaks.so: 8 independent FFMA (or sqrt.approx) chains per thread, "
+                   "2048 threads per SM; 16-byte L1-bypassing loads over half the L2"}
 
 
 def time_to_target(stream_cls=None):
@@ -384,6 +410,59 @@ def run_batched():
                       "L_range": [min(Ls), max(Ls)], "ms_per_cycle": ms,
                       "proposals_per_s": props / (ms / 1000.0), "chains_per_cta": C,
                       "threads_per_cta": thr}))
+
+
+def run_grad():
+    """L=300, 512 torsion vectors: one amh_grad call (energy and dV/ds of all
+    512) timed with CUDA events, then AMH (one cycle on 256 chains) and torch
+    L-BFGS (500 iterations) on the best 32 states, wall-timed."""
+    import torch
+    from paper_2211_03193_gb300 import autograd, synth
+    from paper_2211_03193_gb300.sampler import Sampler
+    w = synth.WORKLOADS["grad_L300_b512"]
+    L, batch = w["L"], w["batch"]
+    n = 2 * L
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    tors = synth.random_torsions(batch, L, seed=w["start_seed"])
+    stream = torch.cuda.Stream()
+    with Sampler(prot, 1, tors[:1], stream=stream) as s:
+        th = torch.tensor(tors, device="cuda")
+        E = torch.empty(batch, dtype=torch.float64, device="cuda")
+        G = torch.empty((batch, n), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(3):
+            s.grad(0, th, E, G)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                s.grad(0, th, E, G)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    chains = 256
+    starts = synth.random_torsions(chains, L, seed=w["start_seed"] + 1)
+    with Sampler(prot, chains, starts) as s:
+        t0 = time.perf_counter()
+        for q in range(11):
+            s.sweeps(0 if q < 10 else 1, 8, 1.0, math.radians(10.0), 1, 3)
+        th_all, E0, _, _ = s.state()
+        best = np.argsort(E0)[:32]
+        t1 = time.perf_counter()
+        thL, EL = autograd.lbfgs_refine(s, torch.tensor(th_all.reshape(chains, n)[best],
+                                                        device="cuda"), iterations=500)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        EL = EL.cpu().numpy()
+    print(json.dumps({"experiment": "grad", "L": L, "batch": batch, "ms_per_call": ms,
+                      "vectors_per_s": batch / (ms / 1000.0),
+                      "pair_gradients_per_s": batch * L * (L - 1) / (ms / 1000.0),
+                      "amh_seconds": t1 - t0, "lbfgs_seconds": t2 - t1,
+                      "best32_energy_before": [float(E0[best].min()), float(E0[best].max())],
+                      "best32_energy_after": [float(EL.min()), float(EL.max())]}))
 
 
 def run_reference(args):
@@ -570,6 +649,13 @@ def run_ours(args):
             "flop_per_eval": FLOP_PER_EVAL,
             "peak_basis": "%d SMs x %d FP32 lanes x 2 (FMA) x %.0f MHz (%s max clock)" % (
                 sm_count, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src)}
+    mp = measured_peaks()  # after the timed region
+    if mp:
+        roof["peak_measured"] = mp["fp32_tflops"]
+        roof["frac_of_measured"] = achieved / mp["fp32_tflops"]
+        evals_s = evals_glob_launch / (g_ms / 1000.0)
+        mp["global_sweep_evals_per_s"] = evals_s
+        mp["frac_of_mufu_bound"] = evals_s / mp["mufu_sqrt_per_s"]  # one square root per term
     out = {"metric": "MH proposals/s", "value": value, "unit": "proposals/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -584,7 +670,7 @@ def run_ours(args):
            "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
            "roofline": roof, "gpu_launches": args.steps * (cyc + 1),
            "best_energy_all_ranks": best_e, "best_rank": best_rank,
-           "clocks": clocks, "e2e": e2e}
+           "clocks": clocks, "e2e": e2e, "measured_peaks": mp}
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, seed=1)
     if not args.no_ttt:
@@ -598,7 +684,8 @@ def run_ours(args):
 def main():
     args = parse()
     if args.experiment:
-        {"schemes": run_schemes, "forms": run_forms, "batched": run_batched}[args.experiment]()
+        {"schemes": run_schemes, "forms": run_forms, "batched": run_batched,
+         "grad": run_grad}[args.experiment]()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -1,8 +1,10 @@
-"""Build libamh.so (the C-ABI library) in-tree for sm_103a with nvcc.
+"""Build libamh.so (the C-ABI library) and libamh_peaks.so (the roofline
+microbenchmarks) in-tree for sm_103a with nvcc.
 
 Each .cu file is compiled to an object in parallel, then linked into
-``paper_2211_03193_gb300/libamh.so``.  Objects go to ``_build/`` (ignored by
-git).  Rebuilds only when a source or header is newer than the library.
+``paper_2211_03193_gb300/libamh.so`` (or ``libamh_peaks.so``).  Objects go to
+``_build/`` (ignored by git).  Rebuilds only when a source or header is newer
+than the libraries.
 """
 from __future__ import annotations
 
@@ -17,8 +19,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libamh.so")
+PEAKS_LIB = os.path.join(PKG, "libamh_peaks.so")
 
 SOURCES = ["amh_api.cu", "amh_global.cu", "amh_local.cu", "amh_misc.cu", "amh_noalloc.cu"]
+PEAKS_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr"]
@@ -32,17 +36,17 @@ def nvcc() -> str:
 
 
 def _deps() -> list[str]:
-    out = [os.path.join(CSRC, s) for s in SOURCES]
+    out = [os.path.join(CSRC, s) for s in SOURCES + PEAKS_SOURCES]
     out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    out.append(os.path.join(INCLUDE, "amh.h"))
+    out += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     out.append(os.path.abspath(__file__))
     return out
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PEAKS_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -61,17 +65,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
         return obj, r.stderr
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(len(SOURCES) + len(PEAKS_SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
     if verbose:
         for _, log in results:
             print(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    objs = [o for o, _ in results]
+    for lib, n0, n1 in ((LIB, 0, len(SOURCES)), (PEAKS_LIB, len(SOURCES), len(objs))):
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs[n0:n1], "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
+        os.replace(tmp, lib)
     with open(os.path.join(BUILD, "ptxas.log"), "w") as f:
         for _, log in results:
             f.write(log)

@@ -79,3 +79,17 @@ def test_null_context_calls_return_estate(lib):
     assert lib.amh_energy(None, None) == 5
     assert lib.amh_sweep(None, 1, 0, 1.0, 0.1, 10, 1, None) == 5
     lib.amh_destroy(None)
+
+
+def test_peaks_library_exports_its_symbol():
+    """libamh_peaks.so (the roofline microbenchmarks) builds and exports what
+    amh_peaks.h declares; nothing runs without a GPU."""
+    from paper_2211_03193_gb300 import build
+    build.build()
+    src = open(os.path.join(ROOT, "include", "amh_peaks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(amh_[a-z_0-9]+)\s*\(", src)))
+    assert names == ["amh_measure_peaks"]
+    lib = ctypes.CDLL(build.PEAKS_LIB)
+    for name in names:
+        assert hasattr(lib, name)

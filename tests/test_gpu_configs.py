@@ -1,7 +1,8 @@
 """Parity at the workload configurations: the FP64 single chain (exact
 trajectory), the bench's L=300 / 1024-chain launch (sampled chains), 64
-proteins of uneven length in one context, and L=500 with 64 bins (FP32
-against the FP64 GPU form).  Expected values come from the oracle only."""
+proteins of uneven length in one context, L=500 with 64 bins (FP32 against
+the FP64 GPU form), and the differentiable L=300 / 512-vector batch.
+Expected values come from the oracle only."""
 import math
 
 import numpy as np
@@ -150,3 +151,58 @@ def test_l500_64bins_fp32_against_fp64(amh, orc):
         e = P.energy(th[c].astype(np.float64))
         assert abs(E64[c] - e) <= 1e-11 * abs(e)
         assert abs(E32[c] - e) <= 1e-5 * abs(e)
+
+
+def test_differentiable_l300_batch512(amh, orc):
+    """L=300, 512 torsion vectors: the FP32 energies and dV/ds of all 512 in
+    one call; sampled vectors against the oracle's FP64 energy and gradient,
+    and sampled components against the oracle's central differences (h =
+    1e-4 rad; the analytic derivative lies between the left and right
+    differences, which differ where a pair distance crosses a bin centre
+    within +-h).  Then the hand-off: a short AMH run, the best 32 states
+    through L-BFGS; every state's energy drops and matches the oracle's at
+    the end."""
+    import torch
+    from paper_2211_03193_gb300 import autograd
+    w = synth.WORKLOADS["grad_L300_b512"]
+    L, batch = w["L"], w["batch"]
+    n = 2 * L
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    tors = synth.random_torsions(batch, L, seed=w["start_seed"])
+    P = orc.Problem(L, prot.p, prot.edges)
+    with amh.Sampler(prot, 1, tors[:1]) as s:
+        th = torch.tensor(tors, device="cuda")
+        E, g = s.grad(0, th)
+        E, g = E.cpu().numpy(), g.cpu().numpy()
+        rng = np.random.default_rng(5)
+        h = 1e-4
+        for b in (0, 1, 200, 511):
+            sb = tors[b].astype(np.float64)
+            Vo, go = P.grad(sb)
+            assert abs(E[b] - Vo) <= 1e-5 * abs(Vo)
+            assert np.linalg.norm(g[b] - go) <= 1e-3 * np.linalg.norm(go)
+            tol_g = 2e-3 * np.linalg.norm(go) / math.sqrt(n)
+            for k in rng.choice(np.arange(1, n - 1), 24, replace=False):
+                sp, sm = sb.copy(), sb.copy()
+                sp[k] += h
+                sm[k] -= h
+                V0, Vp, Vm = P.energy(sb), P.energy(sp), P.energy(sm)
+                right, left = (Vp - V0) / h, (V0 - Vm) / h
+                tol = tol_g + 1e-3 * max(abs(left), abs(right))
+                assert min(left, right) - tol <= g[b][k] <= max(left, right) + tol, (b, k)
+    # hand-off: AMH, then L-BFGS on the best 32 states
+    chains = 256
+    starts = synth.random_torsions(chains, L, seed=w["start_seed"] + 1)
+    with amh.Sampler(prot, chains, starts) as s:
+        for q in range(11):
+            s.sweeps(0 if q < 10 else 1, 8, 1.0, 10 * DEG, 1, 3)
+        th, E0, _, _ = s.state()
+        best = np.argsort(E0)[:32]
+        th0 = torch.tensor(th.reshape(chains, n)[best], device="cuda")
+        thL, EL = autograd.lbfgs_refine(s, th0, iterations=500)
+        EL = EL.cpu().numpy()
+    assert np.all(EL < E0[best])
+    for b in (0, 17, 31):
+        e = P.energy(thL[b].cpu().numpy().astype(np.float64))
+        assert abs(EL[b] - e) <= 1e-5 * abs(e)
