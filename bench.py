@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-overlap", dest="overlap", action="store_false",
+                    help="run the gradient pass after the global sweep instead of beside it")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target measurement")
     ap.add_argument("--experiment", default="", choices=["", "schemes", "forms", "batched", "grad"],
@@ -528,10 +530,14 @@ def run_ours(args):
     prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
                               seed=w["seed"])
     tors = synth.random_torsions(chains, L, seed=w["start_seed"] + 1000 * rank)
-    stream = torch.cuda.Stream()
+    # the sweeps run on a high-priority stream; the gradient pass on a second
+    # one, so its CTAs take the SMs the global sweep leaves idle
+    stream = torch.cuda.Stream(priority=-1)
+    aux = torch.cuda.Stream(priority=0)
     samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
                    stage_table=args.stage, table_texture=args.texture)
+    gsamp = Sampler(prot, 1, tors[:1], precision=w["precision"], stream=aux)
     C, thr, D = samp.launch_config()
     # device table: one 8-byte entry per bin, rows padded to an even bin count
     B = len(synth.edges_by_name(w["bins"])) - 1
@@ -545,10 +551,25 @@ def run_ours(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     sweep_idx = [0]
 
+    def grad_pass():
+        _amh.amh_grad(gsamp.ctx, 0, theta_dev, chains, E_dev, G_dev)
+
     def cycle(glob_events=None):
+        """10 local sweeps and the global sweep on every chain, and the
+        L-BFGS hand-off: dV/ds of every chain's state.  With --overlap (the
+        default) the gradient pass covers the states that ended the previous
+        cycle and runs on the second stream beside the global sweep; the
+        cycle ends when both are done, and then snapshots its end states."""
         for j in range(cyc):
             s = sweep_idx[0] % w["total_sweeps"]
             mode, T, sigma = sched.params(s)
+            if mode == _amh.AMH_GLOBAL and args.overlap:
+                go = torch.cuda.Event()
+                go.record(stream)
+                aux.wait_event(go)
+                grad_pass()
+                done = torch.cuda.Event()
+                done.record(aux)
             if mode == _amh.AMH_GLOBAL and glob_events is not None:
                 e0, e1 = ev(), ev()
                 e0.record(stream)
@@ -557,13 +578,22 @@ def run_ours(args):
                 glob_events.append((e0, e1))
             else:
                 _amh.amh_sweeps(samp.ctx, mode, w["window"], T, sigma, 1, sched.seed, None)
+            if mode == _amh.AMH_GLOBAL and args.overlap:
+                stream.wait_event(done)
             sweep_idx[0] += 1
-        # hand-off: gradient of every chain's current state
         _amh.amh_get_state(samp.ctx, theta_dev, None, None, None)
-        _amh.amh_grad(samp.ctx, 0, theta_dev, chains, E_dev, G_dev)
+        if not args.overlap:
+            go = torch.cuda.Event()
+            go.record(stream)
+            aux.wait_event(go)
+            grad_pass()
+            done = torch.cuda.Event()
+            done.record(aux)
+            stream.wait_event(done)
 
     # the schedule's global sweep is the cycle's last sweep; align to a cycle
     with torch.cuda.stream(stream):
+        _amh.amh_get_state(samp.ctx, theta_dev, None, None, None)
         for _ in range(args.warmup):
             cycle()
     torch.cuda.synchronize()
@@ -627,6 +657,7 @@ def run_ours(args):
         best_e, best_rank = float(np.min(bE_all)), 0
     if rank != 0:
         samp.close()
+        gsamp.close()
         if world > 1:
             dist.destroy_process_group()
         return
@@ -666,6 +697,10 @@ def run_ours(args):
                       "(256 MB write); the %.1f MB table is L2-resident within a step" % (
                           tab_mb,),
                       "chains_per_cta": C, "threads_per_cta": thr, "stage_depth": D,
+                      "gradient": "dV/ds of all %d states once per step (one amh_grad launch); %s" % (
+                          chains, "on a second stream beside the global sweep, over the states "
+                          "that ended the previous step" if args.overlap else
+                          "after the global sweep, over the step's end states"),
                       "parallelism": "independent chains per GPU (replicas)"},
            "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
            "roofline": roof, "gpu_launches": args.steps * (cyc + 1),
@@ -677,6 +712,7 @@ def run_ours(args):
         out["time_to_target"] = time_to_target()
     print(json.dumps(out))
     samp.close()
+    gsamp.close()
     if world > 1:
         dist.destroy_process_group()
 
