@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--far-pairs", type=int, default=0, choices=[0, 1],
+                    help="1: evaluate every straddle pair (no far-field skipping)")
     ap.add_argument("--no-overlap", dest="overlap", action="store_false",
                     help="run the gradient pass after the global sweep instead of beside it")
     ap.add_argument("--no-cpu", action="store_true")
@@ -536,8 +538,10 @@ def run_ours(args):
     aux = torch.cuda.Stream(priority=0)
     samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
-                   stage_table=args.stage, table_texture=args.texture)
-    gsamp = Sampler(prot, 1, tors[:1], precision=w["precision"], stream=aux)
+                   stage_table=args.stage, table_texture=args.texture, far_pairs=args.far_pairs)
+    # a context for the gradient pass only (fixed launch shape: no autotuning)
+    gsamp = Sampler(prot, 1, tors[:1], precision=w["precision"], stream=aux, chains_per_cta=1,
+                    threads_per_cta=128)
     C, thr, D = samp.launch_config()
     # device table: one 8-byte entry per bin, rows padded to an even bin count
     B = len(synth.edges_by_name(w["bins"])) - 1
@@ -601,6 +605,7 @@ def run_ours(args):
         dist.barrier()
     step_ms = []
     glob_ev = []
+    terms0 = samp.pair_terms()  # straddle-pair terms evaluated so far (synchronises)
     with Clocks(local) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
@@ -613,6 +618,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    terms_glob = (samp.pair_terms() - terms0) / args.steps  # per global sweep, this rank
     total_ms = sum(a.elapsed_time(b_) for a, b_ in step_ms)
     glob_ms = [a.elapsed_time(b_) for a, b_ in glob_ev]
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -664,8 +670,12 @@ def run_ours(args):
     pk, src = peaks()
     clocks = clk.summary()
     g_ms = float(np.mean(glob_ms)) if glob_ms else float("nan")
-    L3 = 2 * (L ** 3 - L) // 3 + 2 * (L * (L - 1) // 2)
-    evals_glob_launch = L3 * chains
+    # terms per global launch: the straddle blocks' (all of them with
+    # --far-pairs 1, else those not skipped as flat; counted by the library)
+    # plus the entry and exit resyncs' full energies
+    dense = 2 * (L ** 3 - L) // 3 * chains
+    resync_terms = 2 * (L * (L - 1) // 2) * chains
+    evals_glob_launch = int(terms_glob) + resync_terms
     achieved = evals_glob_launch * FLOP_PER_EVAL / (g_ms / 1000.0) / 1e12
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -677,6 +687,7 @@ def run_ours(args):
                 (", table entries through the texture path" if args.texture != 2
                  else ", table entries through L1 loads")),
             "launch_ms": g_ms, "pair_evals_per_launch": evals_glob_launch,
+            "straddle_terms_dense": dense, "straddle_terms_evaluated": int(terms_glob),
             "flop_per_eval": FLOP_PER_EVAL,
             "peak_basis": "%d SMs x %d FP32 lanes x 2 (FMA) x %.0f MHz (%s max clock)" % (
                 sm_count, FP32_LANES_PER_SM, pk.get("sm_max_mhz", 2070.0), src)}
@@ -702,7 +713,11 @@ def run_ours(args):
                           "that ended the previous step" if args.overlap else
                           "after the global sweep, over the step's end states"),
                       "parallelism": "independent chains per GPU (replicas)"},
-           "pair_evals_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
+           # terms computed per second (global sweeps as counted by the library,
+           # resyncs, local windows), and the dense count of the same work
+           "pair_evals_per_s": (evals_glob_launch + ev_loc * chains) * args.steps * world /
+                               (total_ms / 1000.0),
+           "pair_evals_dense_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
            "roofline": roof, "gpu_launches": args.steps * (cyc + 1),
            "best_energy_all_ranks": best_e, "best_rank": best_rank,
            "clocks": clocks, "e2e": e2e, "measured_peaks": mp}

@@ -59,8 +59,8 @@ typedef struct {
   int chains_per_cta;      /* chains that share one CTA in global sweeps:
                               0 = autotuned at first use, else 1, 2, 4 or 8. */
   int threads_per_cta;     /* global sweeps: 0 = autotuned with chains_per_cta
-                              (256 if chains_per_cta is set), else 128, 256
-                              or 512. */
+                              (256 if chains_per_cta is set), else 64, 128,
+                              256 or 512. */
   int trace_chains;        /* record every proposal of chains [0, trace_chains) */
   long long trace_capacity;/* records kept per traced chain (visit order) */
   int lattice_K;           /* test mode: 0 = off; K > 0 snaps proposals to a
@@ -78,6 +78,12 @@ typedef struct {
                               table fits the device's 1-D texture limit, else
                               global loads (default); 1 = texture (AMH_EINVAL if
                               it does not fit); 2 = global loads. */
+  int far_pairs;           /* precision 32, global sweeps: 0 = skip the straddle
+                              pairs that stay beyond the last bin centre before
+                              and after the move (their Eq. 5 terms are equal,
+                              so Delta V is unchanged; found per 32-atom chunk
+                              of the fixed side by bounding spheres) (default);
+                              1 = evaluate every straddle pair. */
   void* stream;            /* cudaStream_t; NULL = the legacy default stream */
 } amh_options;
 
@@ -223,6 +229,16 @@ amh_status amh_get_trace(amh_ctx* ctx, int chain, amh_trace_rec* out, long long*
 
 /* amh_counter -- the proposal counter t of chain `chain`. */
 amh_status amh_counter(amh_ctx* ctx, int chain, long long* t);
+
+/*
+ * amh_pair_terms -- straddle-pair terms the global sweeps of this context
+ * have evaluated so far (Sec. 2.4 scores every pair of the block a < p(k) <=
+ * b; each term is e(|x_a - x_b|) at one configuration: the current one or a
+ * proposal's).  With far_pairs = 0 the terms of pairs that stay beyond the
+ * last bin centre are skipped and not counted.  *evaluated (host) is
+ * cumulative since amh_init; synchronises the context's stream.
+ */
+amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated);
 
 /*
  * amh_philox -- the sampler's random stream, for checking: for

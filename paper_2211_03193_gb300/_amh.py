@@ -33,7 +33,7 @@ class amh_options(ctypes.Structure):
                 ("trace_chains", ctypes.c_int), ("trace_capacity", ctypes.c_longlong),
                 ("lattice_K", ctypes.c_int), ("table_is_neglog", ctypes.c_int),
                 ("stage_table", ctypes.c_int), ("table_texture", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("far_pairs", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class amh_trace_rec(ctypes.Structure):
@@ -71,6 +71,7 @@ def load() -> ctypes.CDLL:
     L.amh_noisy_restart.argtypes = [vp, ctypes.c_double, ctypes.c_ulonglong]
     L.amh_get_trace.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_longlong)]
     L.amh_counter.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+    L.amh_pair_terms.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
     L.amh_philox.argtypes = [ctypes.c_ulonglong, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_uint,
                              ctypes.c_longlong, vp, vp, vp]
     L.amh_last_error.argtypes = [vp]
@@ -85,7 +86,7 @@ def load() -> ctypes.CDLL:
     for name in ("amh_init", "amh_energy", "amh_sweep", "amh_sweeps", "amh_grad", "amh_get_state",
                  "amh_set_state", "amh_noisy_restart", "amh_get_trace", "amh_counter",
                  "amh_philox", "amh_launch_config", "amh_grad_noalloc", "amh_set_ladder",
-                 "amh_exchange"):
+                 "amh_exchange", "amh_pair_terms"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -203,6 +204,13 @@ def amh_counter(ctx, chain) -> int:
     return t.value
 
 
+def amh_pair_terms(ctx) -> int:
+    """Straddle-pair terms evaluated by the context's global sweeps so far."""
+    v = ctypes.c_ulonglong()
+    _check(load().amh_pair_terms(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
 def amh_philox(seed, chain, t0, stream, count):
     words = np.zeros((count, 4), dtype=np.uint32)
     z = np.zeros(count, dtype=np.float32)
@@ -243,4 +251,4 @@ def amh_grad_noalloc(L, B, table, table_is_neglog, edges, theta, batch, E_out, d
 EXPORTED = ["amh_options_default", "amh_init", "amh_energy", "amh_sweep", "amh_sweeps",
             "amh_grad", "amh_get_state", "amh_set_state", "amh_noisy_restart", "amh_get_trace",
             "amh_counter", "amh_philox", "amh_last_error", "amh_launch_config", "amh_destroy",
-            "amh_grad_noalloc", "amh_set_ladder", "amh_exchange"]
+            "amh_grad_noalloc", "amh_set_ladder", "amh_exchange", "amh_pair_terms"]

@@ -45,6 +45,7 @@ struct amh_ctx {
   int nlgroups[6] = {0, 0, 0, 0, 0, 0};
   int* queue = nullptr;
   int* err = nullptr;
+  unsigned long long* pair_count = nullptr;  // straddle-pair terms evaluated by global sweeps
   TraceRec* trace = nullptr;
   long long* trace_count = nullptr;
   // launch configuration
@@ -145,6 +146,12 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   a.trace_count = ctx->trace_count;
   a.err = ctx->err;
   a.stage_depth = ctx->stage_depth;
+  // last bin centre c0 + (B-1) w: beyond it sat(d k1 + k2) = 1 and the FP32
+  // term is the constant last entry; 0.01 A covers the rounding of the
+  // distances and of the bounding spheres (~1e-5 A)
+  a.far_skip = ctx->precision == 32 && ctx->opt.far_pairs == 0 && ctx->Lmax <= 1024;  // 32 chunk bits
+  a.far_cut = (float)(ctx->c0 + (ctx->B - 1) * ctx->w + 0.01);
+  a.pair_count = ctx->pair_count;
   a.ladder = ctx->ladder_K ? ctx->ladder : nullptr;
   a.ladder_K = ctx->ladder_K;
   return a;
@@ -338,7 +345,7 @@ amh_status check_err_flag(amh_ctx* ctx) {
 template <class R>
 amh_status autotune(amh_ctx* ctx) {
   const int cand_C[4] = {1, 2, 4, 8};
-  const int cand_T[2] = {256, 512};
+  const int cand_T[4] = {64, 128, 256, 512};
   long long* t_scr = nullptr;
   R* th_scr = nullptr;
   R* bt_scr = nullptr;
@@ -363,7 +370,7 @@ amh_status autotune(amh_ctx* ctx) {
     if (C > max_C(ctx->precision)) continue;
     for (int T : cand_T) {
      for (int staged = 0; staged < 2; ++staged) {
-      if (staged && ctx->opt.stage_table == 2) continue;
+      if (staged && (ctx->opt.stage_table == 2 || T < 256)) continue;
       if (!staged && ctx->opt.stage_table == 1) continue;
       const int D = staged ? stage_depth_for(ctx, C, T) : 0;
       if (staged && D == 0) continue;
@@ -557,7 +564,8 @@ void free_ctx(amh_ctx* ctx) {
   if (ctx->tex) cudaDestroyTextureObject(ctx->tex);
   void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
                   ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
-                  ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder};
+                  ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder,
+                  ctx->pair_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 6; ++q)
@@ -586,6 +594,7 @@ void amh_options_default(amh_options* opt) {
   opt->table_is_neglog = 0;
   opt->stage_table = 0;
   opt->table_texture = 0;
+  opt->far_pairs = 0;
   opt->stream = nullptr;
 }
 
@@ -610,13 +619,15 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
     return set_err(nullptr, AMH_EINVAL, "chains_per_cta must be 0, 1, 2, 4 or 8");
   if (o.precision == 64 && o.chains_per_cta == 8)
     return set_err(nullptr, AMH_EINVAL, "precision 64 allows at most 4 chains per CTA");
-  if (o.threads_per_cta != 0 && o.threads_per_cta != 128 && o.threads_per_cta != 256 &&
-      o.threads_per_cta != 512)
-    return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 128, 256 or 512");
+  if (o.threads_per_cta != 0 && o.threads_per_cta != 64 && o.threads_per_cta != 128 &&
+      o.threads_per_cta != 256 && o.threads_per_cta != 512)
+    return set_err(nullptr, AMH_EINVAL, "threads_per_cta must be 0, 64, 128, 256 or 512");
   if (o.table_texture < 0 || o.table_texture > 2)
     return set_err(nullptr, AMH_EINVAL, "table_texture must be 0, 1 or 2");
   if (o.stage_table < 0 || o.stage_table > 2)
     return set_err(nullptr, AMH_EINVAL, "stage_table must be 0, 1 or 2");
+  if (o.far_pairs < 0 || o.far_pairs > 1)
+    return set_err(nullptr, AMH_EINVAL, "far_pairs must be 0 or 1");
   if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)
     return set_err(nullptr, AMH_EINVAL, "negative option");
   // bins: evenly spaced centres
@@ -719,6 +730,8 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   CKI(cudaMalloc(&ctx->queue, sizeof(int)));
   CKI(cudaMalloc(&ctx->err, sizeof(int)));
   CKI(cudaMemset(ctx->err, 0, sizeof(int)));
+  CKI(cudaMalloc(&ctx->pair_count, sizeof(unsigned long long)));
+  CKI(cudaMemset(ctx->pair_count, 0, sizeof(unsigned long long)));
   if (o.trace_chains > 0 && o.trace_capacity > 0) {
     const int tc = std::min(o.trace_chains, nc);
     ctx->opt.trace_chains = tc;
@@ -967,6 +980,16 @@ amh_status amh_counter(amh_ctx* ctx, int chain, long long* t) {
   if (chain < 0 || chain >= ctx->total_chains || !t) return set_err(ctx, AMH_EINVAL, "bad chain");
   CK(ctx, cudaMemcpyAsync(t, ctx->tcount + chain, sizeof(long long), cudaMemcpyDeviceToHost,
                           ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return AMH_OK;
+}
+
+amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!evaluated) return set_err(ctx, AMH_EINVAL, "evaluated is NULL");
+  CK(ctx, cudaMemcpyAsync(evaluated, ctx->pair_count, sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   return AMH_OK;
 }

@@ -37,15 +37,27 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 31) & ~size_t(
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cb, maps, part, ecur, thn, lnu, acc, commit, flag, scan, bars,
-      ring, total;
-  // D ring slots per warp of 32/C rows of RB bytes (D = 0: no staging)
+  size_t theta, bb, cb, maps, list, fsph, bits, part, ecur, thn, lnu, acc, commit, flag, scan,
+      bars, ring, total;
+  int ls;  // stride between chains of the C-beta array (odd: conflict-free 16-byte loads)
+  int nm;  // moving atoms at most: stride of the chunk bits per chain
+  // D ring slots per warp of 32/C rows of RB bytes (D = 0: no staging).  The
+  // FP32 unstaged kernel also holds the far-field pruning's arrays: the kept
+  // items, spheres of the fixed side's chunks, and per (chain, moving atom)
+  // the chunks within reach as bits.
   __host__ __device__ Layout(int Lmax, int nmax, int W, int D = 0, int RB = 0) {
+    const bool far = sizeof(R) == 4 && D == 0;
+    const int nM = (Lmax + 1) / 2, nJ = (Lmax + 31) / 32;
+    nm = nM;
     size_t o = 0;
     theta = o; o = align16(o + sizeof(R) * (size_t)nmax * C);
     bb = o;    o = align16(o + sizeof(R) * (size_t)Lmax * 9 * C);
-    cb = o;    o = align16(o + sizeof(Pt4<R>) * (size_t)Lmax * C);
+    ls = Lmax | 1;
+    cb = o;    o = align16(o + sizeof(Pt4<R>) * (size_t)ls * C);
     maps = o;  o = align16(o + sizeof(R) * 36 * C);
+    list = o;  o = align16(o + (far ? sizeof(unsigned short) * (size_t)nM * nJ : 0));
+    fsph = o;  o = align16(o + (far ? sizeof(Pt4<R>) * (size_t)nJ * C : 0));
+    bits = o;  o = align16(o + (far ? sizeof(unsigned) * (size_t)nM * C : 0));
     part = o;  o = align16(o + sizeof(double) * 3 * (size_t)W * C);
     ecur = o;  o = align16(o + sizeof(double) * C);
     thn = o;   o = align16(o + sizeof(R) * 2 * C);
@@ -65,8 +77,12 @@ template <class R, int C>
 struct Shm {
   R* theta;  // [k][C]
   R* bb;     // [((i*3+atom)*3+xyz)][C], atom 0 N, 1 CA, 2 C
-  Pt4<R>* cb4;  // [i][C]
+  Pt4<R>* cb4;  // [C][ls]: chain-major, odd stride
   R* maps;   // [C][36]: A1, A2, A21
+  unsigned short* list;  // items kept by the far-field test, in order
+  Pt4<R>* fsph;    // [chunk][C]: centre and radius of a fixed-side chunk's C-betas
+  unsigned* bits;  // [C][moving atom]: chunks whose pairs may not be flat
+  int ls, nm;
   double* part;  // [W][C][3]
   double* ecur;  // [C]
   R* thn;        // [2][C]
@@ -82,6 +98,11 @@ struct Shm {
     bb = (R*)(base + l.bb);
     cb4 = (Pt4<R>*)(base + l.cb);
     maps = (R*)(base + l.maps);
+    list = (unsigned short*)(base + l.list);
+    fsph = (Pt4<R>*)(base + l.fsph);
+    bits = (unsigned*)(base + l.bits);
+    ls = l.ls;
+    nm = l.nm;
     part = (double*)(base + l.part);
     ecur = (double*)(base + l.ecur);
     thn = (R*)(base + l.thn);
@@ -94,7 +115,7 @@ struct Shm {
     ring = base + l.ring;
   }
   __device__ V3<R> cb(int i, int c) const {
-    const Pt4<R> p = cb4[i * C + c];
+    const Pt4<R> p = cb4[c * ls + i];
     return v3<R>(p.x, p.y, p.z);
   }
   __device__ void set_cb(int i, int c, V3<R> v) {
@@ -103,7 +124,7 @@ struct Shm {
     p.y = v.y;
     p.z = v.z;
     p.w = (R)0;
-    cb4[i * C + c] = p;
+    cb4[c * ls + i] = p;
   }
   __device__ V3<R> atom(int i, int a, int c) const {
     const R* p = bb + (size_t)((i * 3 + a) * 3) * C + c;
@@ -218,18 +239,22 @@ __device__ __forceinline__ void store_aff(R* dst, const Aff<R>& A) {
 }
 
 // Straddle-block Delta-E (moving side [m0, m1), fixed side [f0, f1)).
-template <class R, int C, bool FUSED, bool TEX>
+// Items are (moving atom, chunk of kFC fixed atoms); with LIST the items
+// run are the nlist entries of `list` (item indices mi * nch + ch).
+template <class R, int C, bool FUSED, bool TEX, bool LIST = false>
 __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, int L, int m0,
-                           int m1, int f0, int f1) {
+                           int m1, int f0, int f1, const unsigned short* list = nullptr,
+                           int nlist = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   constexpr int S = 32 / C;
   const int c = lane % C, sl = lane / C;
   const int gs = warp * S + sl, G = W * S;
   const int nF = f1 - f0;
   const int nch = (nF + kFC - 1) / kFC;
-  const int items = (m1 - m0) * nch;
+  const int items = LIST ? nlist : (m1 - m0) * nch;
   typename AccT<R>::T acc1 = 0, acc2 = 0, acc21 = 0;
-  for (int it = gs; it < items; it += G) {
+  for (int q = gs; q < items; q += G) {
+    const int it = LIST ? (int)list[q] : q;
     const int mi = it / nch, ch = it - mi * nch;
     const int m = m0 + mi;
     const V3<R> xm = s.cb(m, c);
@@ -284,6 +309,136 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     }
   }
   reduce3(s, (double)acc1, (double)acc2, (double)acc21);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float dist2(V3<float> a, V3<float> b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+__device__ __forceinline__ V3<float> v3of(Pt4<float> p) { return v3<float>(p.x, p.y, p.z); }
+__device__ __forceinline__ Pt4<float> pt4of(V3<float> v) {
+  Pt4<float> p;
+  p.x = v.x;
+  p.y = v.y;
+  p.z = v.z;
+  p.w = 0.f;
+  return p;
+}
+
+// The straddle block without its flat far field (FP32).  Beyond the last
+// bin centre the Eq. 5 term is the constant -ln p of the last bin, so a pair
+// whose distance is past it before and after the move adds exactly zero to
+// Delta-E.  Per chain, the fixed side is cut into the kFC-atom chunks of the
+// pair loop with bounding spheres, and each moving atom's images (the atom
+// under A1, A2, A21) get one too; an item (moving atom, chunk) is run when
+// the two spheres come within `cut` (the last centre plus a margin for
+// rounding) for any chain of the CTA.  The kept items, listed in order, go
+// through the same pair loop as the full block.
+template <int C, bool FUSED, bool TEX>
+__device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long tab_off, int L,
+                               int m0, int m1, int f0, int f1, float cut, unsigned real,
+                               unsigned long long& count) {
+  static_assert(kFC == 32, "one bit per chunk of a 32-bit word");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int nM = m1 - m0, nJ = (f1 - f0 + kFC - 1) / kFC;
+  const int nMs = s.nm;  // stride of s.bits per chain
+  // (1) one thread per (chunk, chain): the bounding box's centre and the
+  // largest distance from it
+  for (int t = threadIdx.x; t < nJ * C; t += blockDim.x) {
+    const int j = t / C, c = t - j * C;
+    const int fb = f0 + kFC * j, fe = min(fb + kFC, f1);
+    V3<float> lo = s.cb(fb, c), hi = lo;
+    for (int f = fb + 1; f < fe; ++f) {
+      const V3<float> x = s.cb(f, c);
+      lo = v3<float>(fminf(lo.x, x.x), fminf(lo.y, x.y), fminf(lo.z, x.z));
+      hi = v3<float>(fmaxf(hi.x, x.x), fmaxf(hi.y, x.y), fmaxf(hi.z, x.z));
+    }
+    const V3<float> o = (lo + hi) * 0.5f;
+    float r2 = 0.f;
+    for (int f = fb; f < fe; ++f) r2 = fmaxf(r2, dist2(s.cb(f, c), o));
+    Pt4<float> q = pt4of(o);
+    q.w = sqrtf(r2);
+    s.fsph[j * C + c] = q;
+  }
+  __syncthreads();
+  // (2) one thread per (moving atom, chain): the images' sphere and the
+  // chunks within reach, as bits
+  for (int t = threadIdx.x; t < nM * C; t += blockDim.x) {
+    const int mi = t / C, c = t - mi * C;
+    unsigned b = 0;
+    if ((real >> c) & 1u) {
+      const V3<float> xm = s.cb(m0 + mi, c);
+      Aff<float> A;
+      load_aff<float, C>(s.maps + 36 * c, A);
+      const V3<float> y1 = apply(A, xm);
+      V3<float> o;
+      float r2;
+      if (FUSED) {
+        load_aff<float, C>(s.maps + 36 * c + 12, A);
+        const V3<float> y2 = apply(A, xm);
+        load_aff<float, C>(s.maps + 36 * c + 24, A);
+        const V3<float> y21 = apply(A, xm);
+        o = (xm + y1 + y2 + y21) * 0.25f;
+        r2 = fmaxf(fmaxf(dist2(xm, o), dist2(y1, o)), fmaxf(dist2(y2, o), dist2(y21, o)));
+      } else {
+        o = (xm + y1) * 0.5f;
+        r2 = fmaxf(dist2(xm, o), dist2(y1, o));
+      }
+      const float reach = sqrtf(r2) + cut;
+      for (int j = 0; j < nJ; ++j) {
+        const Pt4<float> q = s.fsph[j * C + c];
+        const float lim = reach + q.w;
+        if (dist2(o, v3of(q)) < lim * lim) b |= 1u << j;
+      }
+    }
+    s.bits[c * nMs + mi] = b;
+  }
+  __syncthreads();
+  // (3) the items kept for any chain, in item order (a block-wide scan of
+  // their counts per moving atom)
+  auto kept = [&](int mi) {
+    unsigned w = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) w |= s.bits[c * nMs + mi];
+    return w;
+  };
+  const int per = (nM + blockDim.x - 1) / blockDim.x;
+  const int b0 = min(nM, (int)threadIdx.x * per), b1 = min(nM, b0 + per);
+  int mine = 0;
+  for (int mi = b0; mi < b1; ++mi) mine += __popc(kept(mi));
+  int incl = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += o;
+  }
+  int* wsum = reinterpret_cast<int*>(s.scan);  // warp totals (the scan area is free here)
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int base = 0, total = 0;
+  for (int w = 0; w < W; ++w) {
+    const int v = wsum[w];
+    if (w < warp) base += v;
+    total += v;
+  }
+  int q = base + incl - mine;
+  for (int mi = b0; mi < b1; ++mi) {
+    unsigned w = kept(mi);
+    while (w) {
+      const int j = __ffs(w) - 1;
+      w &= w - 1;
+      s.list[q++] = (unsigned short)(mi * nJ + j);
+      count += (unsigned long long)min(kFC, f1 - f0 - kFC * j) * __popc(real) * (FUSED ? 4 : 2);
+    }
+  }
+  __syncthreads();
+  // (4) the kept items through the full block's pair loop
+  pair_block<float, C, FUSED, TEX, true>(s, tb, tab_off, L, m0, m1, f0, f1, s.list, total);
 }
 
 // The straddle block with its table rows staged in shared memory.  Each warp
@@ -525,6 +680,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
   resync(s, a, P);
   long long since = 0;
+  const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
+  unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
   for (long long j = 0; j < steps;) {
     if (since >= a.resync_every) {
       resync(s, a, P);
@@ -605,7 +762,23 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
                                               a.stage_depth, par, a.err);
       if (!ok) *(volatile int*)abort_flag = 1;
     } else if constexpr (sizeof(R) == 4) {
-      if (a.tab.tex) {
+      if (a.far_skip) {
+        if (a.tab.tex) {
+          if (fused)
+            pair_block_far<C, true, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
+                                          count);
+          else
+            pair_block_far<C, false, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
+                                           count);
+        } else {
+          if (fused)
+            pair_block_far<C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
+                                           count);
+          else
+            pair_block_far<C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
+                                            count);
+        }
+      } else if (a.tab.tex) {
         if (fused)
           pair_block<R, C, true, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
         else
@@ -622,6 +795,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       else
         pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
     }
+    if (threadIdx.x == 0 && !(sizeof(R) == 4 && !ST && a.far_skip))
+      count += (unsigned long long)(m1 - m0) * (f1 - f0) * min(G.nchains, C) * (fused ? 4 : 2);
     __syncthreads();
     if (*(volatile int*)abort_flag) break;  // a staging wait gave up: stop (flagged)
     if (threadIdx.x < C) {
@@ -665,6 +840,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   }
   resync(s, a, P);
   store_group(s, a, G, P, t0 + steps, true);
+  if (a.pair_count && count) atomicAdd(a.pair_count, count);
 }
 
 template <class R, int C, bool ST>

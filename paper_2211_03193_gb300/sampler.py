@@ -25,7 +25,7 @@ class Sampler:
     def __init__(self, proteins, chains, torsions, precision: int = 32, resync_every: int = 1000,
                  chains_per_cta: int = 0, threads_per_cta: int = 0, trace_chains: int = 0,
                  trace_capacity: int = 0, lattice_K: int = 0, stage_table: int = 0,
-                 table_texture: int = 0, stream=None):
+                 table_texture: int = 0, far_pairs: int = 0, stream=None):
         if not isinstance(proteins, (list, tuple)):
             proteins = [proteins]
         chains = list(np.atleast_1d(chains).astype(int))
@@ -55,7 +55,7 @@ class Sampler:
                                        threads_per_cta=threads_per_cta, trace_chains=trace_chains,
                                        trace_capacity=trace_capacity, lattice_K=lattice_K,
                                        stage_table=stage_table, table_texture=table_texture,
-                                       stream=stream)
+                                       far_pairs=far_pairs, stream=stream)
         self.ctx = _amh.amh_init(np.array(self.L), np.array(chains), torsions, table, edges, opt)
         self.precision = precision
 
@@ -125,6 +125,10 @@ class Sampler:
             dE = torch.empty_like(theta)
         _amh.amh_grad(self.ctx, protein, theta, batch, E_out, dE)
         return E_out, dE
+
+    def pair_terms(self) -> int:
+        """Straddle-pair terms the global sweeps have evaluated so far."""
+        return _amh.amh_pair_terms(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -207,6 +207,43 @@ def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads, te
         assert np.all(bE <= E + 1e-9)
 
 
+@pytest.mark.parametrize("C", [8, 2])
+def test_far_field_skip_equals_dense(amh, orc, C):
+    """FP32 global sweeps with the flat far field skipped (the default) and
+    with every straddle pair evaluated, from the same states and seeds: the
+    same Delta-E within FP32 rounding of the different summation order, the
+    same decisions up to the first near-tie, and oracle parity (teacher-forced
+    replay) for the skipping run.  L=150 from random starts, so most
+    (moving atom, chunk) items are far."""
+    L, chains = 150, 16
+    prot = synth.make_protein(L, seed=305)
+    tors = synth.random_torsions(chains, L, seed=306)
+    n = 2 * L
+    steps = n + 3
+    T, sigma, seed = 0.6, 10 * DEG, 41
+    runs = []
+    for far in (0, 1):
+        # frequent resyncs keep the FP32 commits' drift inside the replay's
+        # tolerance at this length
+        with amh.Sampler(prot, chains, tors, chains_per_cta=C, far_pairs=far, resync_every=60,
+                         trace_chains=chains, trace_capacity=steps) as s:
+            s.sweep(1, 0, T, sigma, steps, seed)
+            runs.append(([s.trace(c) for c in range(chains)], s.state()[1]))
+    (tf, Ef), (td, Ed) = runs
+    k = tf[0]["k"]
+    p = (k + 1) // 2
+    npairs = p * (L - p)
+    for c in range(chains):
+        split = np.flatnonzero(tf[c]["accept"] != td[c]["accept"])
+        upto = split[0] + 1 if split.size else steps
+        d = np.abs(tf[c]["dE"][:upto] - td[c]["dE"][:upto])
+        assert np.all(d <= de_tol(npairs[:upto], td[c]["dE"][:upto])), c
+        if split.size:
+            assert abs(td[c]["lnu"][split[0]] + td[c]["dE"][split[0]] / T) <= 1e-3
+    for c in (0, 7, 15):
+        replay_and_compare(orc, prot, tors[c], tf[c], orc.GLOBAL, 0, T, sigma, 0, seed, c, False)
+
+
 def test_global_fp64_untouched_trajectory_equals_oracle(amh, orc):
     """FP64 GPU vs oracle without teacher forcing: identical decisions."""
     L = 24
