@@ -179,6 +179,25 @@ __device__ __forceinline__ void reduce3(Shm<R, C>& s, double a0, double a1, doub
   }
 }
 
+// The same for the straddle blocks' partial sums, in FP32 (each partial is
+// an FP32 sum already; the FP64 pipe is the scarce one): results in s.part.
+template <class R, int C>
+__device__ __forceinline__ void reduce3f(Shm<R, C>& s, float a0, float a1, float a2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = C; off < 32; off <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+  }
+  if (lane < C) {
+    double* p = s.part + (size_t)(warp * C + lane) * 3;
+    p[0] = a0;
+    p[1] = a1;
+    p[2] = a2;
+  }
+}
+
 // Full energy of every chain slot from the current coordinates: FP32 (or
 // FP64) pair terms, FP64 sums (Eq. 5 over a<b).  Ends with s.ecur set.
 template <class R, int C>
@@ -308,7 +327,10 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
       step += dstep;
     }
   }
-  reduce3(s, (double)acc1, (double)acc2, (double)acc21);
+  if constexpr (sizeof(R) == 4)
+    reduce3f(s, acc1, acc2, acc21);
+  else
+    reduce3(s, (double)acc1, (double)acc2, (double)acc21);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -838,7 +860,15 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     j += fused ? 2 : 1;
     since += fused ? 2 : 1;
   }
-  resync(s, a, P);
+  // exit: the energy from scratch (FP64 sum); the FP32 form takes the
+  // current coordinates (their drift since the entry rebuild is ~1e-5 A),
+  // the FP64 form rebuilds G(s) as well
+  if constexpr (sizeof(R) == 4) {
+    __syncthreads();
+    full_energy(s, a.tab, P.tab_off, L);
+  } else {
+    resync(s, a, P);
+  }
   store_group(s, a, G, P, t0 + steps, true);
   if (a.pair_count && count) atomicAdd(a.pair_count, count);
 }
