@@ -149,7 +149,9 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   // last bin centre c0 + (B-1) w: beyond it sat(d k1 + k2) = 1 and the FP32
   // term is the constant last entry; 0.01 A covers the rounding of the
   // distances and of the bounding spheres (~1e-5 A)
-  a.far_skip = ctx->precision == 32 && ctx->opt.far_pairs == 0 && ctx->Lmax <= 1024;  // 32 chunk bits
+  // the chunks of a fixed side are bits of one word
+  a.far_skip = ctx->precision == 32 && ctx->opt.far_pairs == 0 &&
+               ctx->Lmax <= kMaxChunks * kPairChunk + 1;
   a.far_cut = (float)(ctx->c0 + (ctx->B - 1) * ctx->w + 0.01);
   a.pair_count = ctx->pair_count;
   a.ladder = ctx->ladder_K ? ctx->ladder : nullptr;

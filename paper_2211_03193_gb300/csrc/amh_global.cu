@@ -18,7 +18,7 @@ namespace amh {
 
 namespace {
 
-constexpr int kFC = 32;  // fixed-side atoms per work item
+constexpr int kFC = kPairChunk;  // fixed-side atoms per work item
 
 template <class R>
 struct AccT {
@@ -37,7 +37,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 31) & ~size_t(
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cb, maps, list, fsph, bits, part, ecur, thn, lnu, acc, commit, flag, scan,
+  size_t theta, bb, cb, maps, list, fsph, bits, part, partf, ecur, thn, lnu, acc, commit, flag, scan,
       bars, ring, total;
   int ls;  // stride between chains of the C-beta array (odd: conflict-free 16-byte loads)
   int nm;  // moving atoms at most: stride of the chunk bits per chain
@@ -47,7 +47,7 @@ struct Layout {
   // the chunks within reach as bits.
   __host__ __device__ Layout(int Lmax, int nmax, int W, int D = 0, int RB = 0) {
     const bool far = sizeof(R) == 4 && D == 0;
-    const int nM = (Lmax + 1) / 2, nJ = (Lmax + 31) / 32;
+    const int nM = (Lmax + 1) / 2, nJ = (Lmax + kFC - 1) / kFC;
     nm = nM;
     size_t o = 0;
     theta = o; o = align16(o + sizeof(R) * (size_t)nmax * C);
@@ -57,8 +57,9 @@ struct Layout {
     maps = o;  o = align16(o + sizeof(R) * 36 * C);
     list = o;  o = align16(o + (far ? sizeof(unsigned short) * (size_t)nM * nJ : 0));
     fsph = o;  o = align16(o + (far ? sizeof(Pt4<R>) * (size_t)nJ * C : 0));
-    bits = o;  o = align16(o + (far ? sizeof(unsigned) * (size_t)nM * C : 0));
+    bits = o;  o = align16(o + (far ? sizeof(ChunkBits) * (size_t)nM * C : 0));
     part = o;  o = align16(o + sizeof(double) * 3 * (size_t)W * C);
+    partf = o; o = align16(o + sizeof(float) * 3 * (size_t)W * C);
     ecur = o;  o = align16(o + sizeof(double) * C);
     thn = o;   o = align16(o + sizeof(R) * 2 * C);
     lnu = o;   o = align16(o + sizeof(R) * 2 * C);
@@ -81,9 +82,10 @@ struct Shm {
   R* maps;   // [C][36]: A1, A2, A21
   unsigned short* list;  // items kept by the far-field test, in order
   Pt4<R>* fsph;    // [chunk][C]: centre and radius of a fixed-side chunk's C-betas
-  unsigned* bits;  // [C][moving atom]: chunks whose pairs may not be flat
+  ChunkBits* bits;  // [C][moving atom]: chunks whose pairs may not be flat
   int ls, nm;
-  double* part;  // [W][C][3]
+  double* part;  // [W][C][3]: FP64 partial sums (energies; FP64 Delta-E)
+  float* partf;  // [W][C][3]: FP32 partial sums of Delta-E
   double* ecur;  // [C]
   R* thn;        // [2][C]
   R* lnu;        // [2][C]
@@ -100,10 +102,11 @@ struct Shm {
     maps = (R*)(base + l.maps);
     list = (unsigned short*)(base + l.list);
     fsph = (Pt4<R>*)(base + l.fsph);
-    bits = (unsigned*)(base + l.bits);
+    bits = (ChunkBits*)(base + l.bits);
     ls = l.ls;
     nm = l.nm;
     part = (double*)(base + l.part);
+    partf = (float*)(base + l.partf);
     ecur = (double*)(base + l.ecur);
     thn = (R*)(base + l.thn);
     lnu = (R*)(base + l.lnu);
@@ -180,7 +183,7 @@ __device__ __forceinline__ void reduce3(Shm<R, C>& s, double a0, double a1, doub
 }
 
 // The same for the straddle blocks' partial sums, in FP32 (each partial is
-// an FP32 sum already; the FP64 pipe is the scarce one): results in s.part.
+// an FP32 sum already; the FP64 pipe is the scarce one): results in s.partf.
 template <class R, int C>
 __device__ __forceinline__ void reduce3f(Shm<R, C>& s, float a0, float a1, float a2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -191,7 +194,7 @@ __device__ __forceinline__ void reduce3f(Shm<R, C>& s, float a0, float a1, float
     a2 += __shfl_xor_sync(0xffffffffu, a2, off);
   }
   if (lane < C) {
-    double* p = s.part + (size_t)(warp * C + lane) * 3;
+    float* p = s.partf + (size_t)(warp * C + lane) * 3;
     p[0] = a0;
     p[1] = a1;
     p[2] = a2;
@@ -365,7 +368,6 @@ template <int C, bool FUSED, bool TEX>
 __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long tab_off, int L,
                                int m0, int m1, int f0, int f1, float cut, unsigned real,
                                unsigned long long& count) {
-  static_assert(kFC == 32, "one bit per chunk of a 32-bit word");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int nM = m1 - m0, nJ = (f1 - f0 + kFC - 1) / kFC;
   const int nMs = s.nm;  // stride of s.bits per chain
@@ -392,7 +394,7 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   // chunks within reach, as bits
   for (int t = threadIdx.x; t < nM * C; t += blockDim.x) {
     const int mi = t / C, c = t - mi * C;
-    unsigned b = 0;
+    ChunkBits b = 0;
     if ((real >> c) & 1u) {
       const V3<float> xm = s.cb(m0 + mi, c);
       Aff<float> A;
@@ -415,7 +417,7 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
       for (int j = 0; j < nJ; ++j) {
         const Pt4<float> q = s.fsph[j * C + c];
         const float lim = reach + q.w;
-        if (dist2(o, v3of(q)) < lim * lim) b |= 1u << j;
+        if (dist2(o, v3of(q)) < lim * lim) b |= ChunkBits(1) << j;
       }
     }
     s.bits[c * nMs + mi] = b;
@@ -424,7 +426,7 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   // (3) the items kept for any chain, in item order (a block-wide scan of
   // their counts per moving atom)
   auto kept = [&](int mi) {
-    unsigned w = 0;
+    ChunkBits w = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c) w |= s.bits[c * nMs + mi];
     return w;
@@ -432,7 +434,7 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   const int per = (nM + blockDim.x - 1) / blockDim.x;
   const int b0 = min(nM, (int)threadIdx.x * per), b1 = min(nM, b0 + per);
   int mine = 0;
-  for (int mi = b0; mi < b1; ++mi) mine += __popc(kept(mi));
+  for (int mi = b0; mi < b1; ++mi) mine += __popcll(kept(mi));
   int incl = mine;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -450,9 +452,9 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   }
   int q = base + incl - mine;
   for (int mi = b0; mi < b1; ++mi) {
-    unsigned w = kept(mi);
+    ChunkBits w = kept(mi);
     while (w) {
-      const int j = __ffs(w) - 1;
+      const int j = __ffsll((long long)w) - 1;
       w &= w - 1;
       s.list[q++] = (unsigned short)(mi * nJ + j);
       count += (unsigned long long)min(kFC, f1 - f0 - kFC * j) * __popc(real) * (FUSED ? 4 : 2);
@@ -600,7 +602,7 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
       par ^= 1u << slot;
     }
   }
-  reduce3(s, (double)acc1, (double)acc2, (double)acc21);
+  reduce3f(s, acc1, acc2, acc21);
   return ok;
 }
 
@@ -825,12 +827,26 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       const int c = threadIdx.x;
       const int chain = G.chain0 + c;
       const int W = blockDim.x >> 5;
-      double d1 = 0.0, d2 = 0.0, d21 = 0.0;
-      for (int w = 0; w < W; ++w) {
-        const double* pp = s.part + (size_t)(w * C + c) * 3;
-        d1 += pp[0];
-        d2 += pp[1];
-        d21 += pp[2];
+      double d1, d2, d21;
+      if constexpr (sizeof(R) == 4) {  // FP32 partials, summed over the warps in FP32
+        float f1 = 0.f, f2 = 0.f, f21 = 0.f;
+        for (int w = 0; w < W; ++w) {
+          const float* pp = s.partf + (size_t)(w * C + c) * 3;
+          f1 += pp[0];
+          f2 += pp[1];
+          f21 += pp[2];
+        }
+        d1 = f1;
+        d2 = f2;
+        d21 = f21;
+      } else {
+        d1 = d2 = d21 = 0.0;
+        for (int w = 0; w < W; ++w) {
+          const double* pp = s.part + (size_t)(w * C + c) * 3;
+          d1 += pp[0];
+          d2 += pp[1];
+          d21 += pp[2];
+        }
       }
       const double Tc = chain_T(a, P, chain);
       // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE (no division)

@@ -41,6 +41,12 @@ inline Geom<R> ideal_geometry() {
 void set_context_free_error(const std::string& m);
 
 // Arguments of a sweep / energy launch over chain groups.
+// Fixed-side atoms per item of the global sweeps' pair loop, and per
+// bounding sphere of the far-field test (one bit per chunk in a 64-bit word).
+constexpr int kPairChunk = 12;
+using ChunkBits = unsigned long long;
+constexpr int kMaxChunks = 64;
+
 template <class R>
 struct SweepArgs {
   const ProteinDev* prot;
