@@ -608,14 +608,18 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
 
 // Apply each chain's committed map to its moving residues [m0, m1).
 template <class R, int C>
-__device__ void commit_moves(Shm<R, C>& s, int m0, int m1) {
-  const int total = (m1 - m0) * 4 * C;
+__device__ void commit_moves(Shm<R, C>& s, int m0, int m1, bool cb_only) {
+  // cb_only: the upstream side moved; the rest of this sweep rotates about
+  // bonds at or after the pivot and never reads these residues' backbone
+  // atoms (a new sweep starts from a rebuild), so only the C-betas move
+  const int per = cb_only ? 1 : 4;
+  const int total = (m1 - m0) * per * C;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int c = idx % C;
     const int code = s.commit[c];
     if (!code) continue;
     const int rest = idx / C;
-    const int atom = rest & 3, i = m0 + (rest >> 2);
+    const int atom = cb_only ? 3 : rest & 3, i = m0 + (cb_only ? rest : rest >> 2);
     Aff<R> A;
     load_aff<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
     if (atom < 3) {
@@ -707,12 +711,14 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
   unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
   for (long long j = 0; j < steps;) {
-    if (since >= a.resync_every) {
+    const long long t = t0 + j;
+    const int k = (int)(t % n);
+    // periodic rebuild, and one at each new sweep inside a call (commits of
+    // upstream moves leave backbone atoms behind, see commit_moves)
+    if (since >= a.resync_every || (k == 0 && j > 0)) {
       resync(s, a, P);
       since = 0;
     }
-    const long long t = t0 + j;
-    const int k = (int)(t % n);
     const bool fused = (k & 1) && (k + 1 < n) && (j + 1 < steps);
     const int p = (k + 1) >> 1;
     const bool up = p <= L - p;  // move the upstream side (it is the smaller)
@@ -871,7 +877,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       s.commit[c] = code;
     }
     __syncthreads();
-    commit_moves(s, m0, m1);
+    commit_moves(s, m0, m1, up);
     __syncthreads();
     j += fused ? 2 : 1;
     since += fused ? 2 : 1;
