@@ -363,11 +363,18 @@ amh_status autotune(amh_ctx* ctx) {
   CK(ctx, cudaEventCreate(&e1));
   float best_ms = 1e30f;
   int bestC = 0, bestT = 256, bestD = 0;
-  const long long steps = 64;
-  std::vector<long long> tstart(ctx->total_chains);
-  for (int p = 0; p < ctx->nprot; ++p)
-    for (int c = 0; c < ctx->nch[p]; ++c)
-      tstart[ctx->prot_h[p].chain0 + c] = std::max(0, ctx->prot_h[p].n / 2 - 32);
+  // three runs of up to 64 proposals, at 1/6, 1/2 and 5/6 of each sweep:
+  // the straddle blocks there have the sizes a whole sweep averages over
+  const long long steps = std::min(64, std::max(2, ctx->nmax / 3));
+  std::vector<long long> tstart[3];
+  for (int seg = 0; seg < 3; ++seg) {
+    tstart[seg].resize(ctx->total_chains);
+    for (int p = 0; p < ctx->nprot; ++p) {
+      const long long n = ctx->prot_h[p].n;
+      const long long at = std::max(0LL, n * (2 * seg + 1) / 6 - steps / 2) & ~1LL;
+      for (int c = 0; c < ctx->nch[p]; ++c) tstart[seg][ctx->prot_h[p].chain0 + c] = at;
+    }
+  }
   for (int C : cand_C) {
     if (C > max_C(ctx->precision)) continue;
     for (int T : cand_T) {
@@ -382,10 +389,11 @@ amh_status autotune(amh_ctx* ctx) {
       amh_status st = configure_global<R>(ctx, C, T, D);
       if (st) return st;
       float ms_sum = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
+      for (int run = 0; run < 4; ++run) {  // run 0 warms up, runs 1-3 are timed
+        const int seg = run == 0 ? 1 : run - 1;
         CK(ctx, cudaMemcpyAsync(th_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(ctx, cudaMemcpyAsync(bt_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(ctx, cudaMemcpyAsync(t_scr, tstart.data(), sizeof(long long) * ctx->total_chains,
+        CK(ctx, cudaMemcpyAsync(t_scr, tstart[seg].data(), sizeof(long long) * ctx->total_chains,
                                 cudaMemcpyHostToDevice, ctx->stream));
         CK(ctx, cudaMemsetAsync(be_scr, 0x7f, sizeof(double) * ctx->total_chains, ctx->stream));
         SweepArgs<R> a = make_args<R>(ctx);
@@ -409,7 +417,7 @@ amh_status autotune(amh_ctx* ctx) {
         CK(ctx, cudaEventSynchronize(e1));
         float ms = 0.f;
         CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
-        if (rep) ms_sum += ms;  // first run warms up
+        if (run) ms_sum += ms;
       }
       if (ms_sum < best_ms) {
         best_ms = ms_sum;

@@ -19,6 +19,7 @@ namespace amh {
 namespace {
 
 constexpr int kFC = kPairChunk;  // fixed-side atoms per work item
+constexpr int kDraw = 64;          // proposals whose draws are made ahead, all at once
 
 template <class R>
 struct AccT {
@@ -37,7 +38,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 31) & ~size_t(
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cb, maps, list, fsph, bits, part, partf, ecur, thn, lnu, acc, commit, flag, scan,
+  size_t theta, bb, cb, draws, maps, list, fsph, bits, part, partf, ecur, thn, lnu, acc, commit, flag, scan,
       bars, ring, total;
   int ls;  // stride between chains of the C-beta array (odd: conflict-free 16-byte loads)
   int nm;  // moving atoms at most: stride of the chunk bits per chain
@@ -54,6 +55,7 @@ struct Layout {
     bb = o;    o = align16(o + sizeof(R) * (size_t)Lmax * 9 * C);
     ls = Lmax | 1;
     cb = o;    o = align16(o + sizeof(Pt4<R>) * (size_t)ls * C);
+    draws = o; o = align16(o + sizeof(R) * 2 * kDraw * C);
     maps = o;  o = align16(o + sizeof(R) * 36 * C);
     list = o;  o = align16(o + (far ? sizeof(unsigned short) * (size_t)nM * nJ : 0));
     fsph = o;  o = align16(o + (far ? sizeof(Pt4<R>) * (size_t)nJ * C : 0));
@@ -79,6 +81,7 @@ struct Shm {
   R* theta;  // [k][C]
   R* bb;     // [((i*3+atom)*3+xyz)][C], atom 0 N, 1 CA, 2 C
   Pt4<R>* cb4;  // [C][ls]: chain-major, odd stride
+  R* draws;     // [kDraw][C][2]: (z, ln u) of the next proposals
   R* maps;   // [C][36]: A1, A2, A21
   unsigned short* list;  // items kept by the far-field test, in order
   Pt4<R>* fsph;    // [chunk][C]: centre and radius of a fixed-side chunk's C-betas
@@ -99,6 +102,7 @@ struct Shm {
     theta = (R*)(base + l.theta);
     bb = (R*)(base + l.bb);
     cb4 = (Pt4<R>*)(base + l.cb);
+    draws = (R*)(base + l.draws);
     maps = (R*)(base + l.maps);
     list = (unsigned short*)(base + l.list);
     fsph = (Pt4<R>*)(base + l.fsph);
@@ -710,7 +714,25 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   long long since = 0;
   const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
   unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
+  long long d0 = 0, dend = 0;  // proposals [d0, dend) have their draws in s.draws
   for (long long j = 0; j < steps;) {
+    if (j + 2 > dend) {
+      // the Philox draws of the next kDraw proposals, by all threads (they
+      // depend on the counter only): the serial step keeps the rotations
+      __syncthreads();
+      d0 = j;
+      dend = j + kDraw;
+      for (int idx = threadIdx.x; idx < kDraw * C; idx += blockDim.x) {
+        const int q = idx / C, c = idx - q * C;
+        R z, lnu;
+        normal_and_lnu(draw_words(a.seed, (uint32_t)(G.chain0 + c),
+                                  (unsigned long long)(t0 + j + q), 0u),
+                       &z, &lnu);
+        s.draws[2 * idx] = z;
+        s.draws[2 * idx + 1] = lnu;
+      }
+      __syncthreads();
+    }
     const long long t = t0 + j;
     const int k = (int)(t % n);
     // periodic rebuild, and one at each new sweep inside a call (commits of
@@ -728,8 +750,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     if (threadIdx.x < C) {
       const int c = threadIdx.x;
       const int chain = G.chain0 + c;
-      R z, lnu;
-      normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)t, 0u), &z, &lnu);
+      const R z = s.draws[2 * ((j - d0) * C + c)], lnu = s.draws[2 * ((j - d0) * C + c) + 1];
       const R th = s.theta[k * C + c];
       const R thn = propose(th, z, a.sigma, a.lattice_K);
       s.thn[c] = thn;
@@ -749,9 +770,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         const Aff<R> A1 = rotation(P1, Q1, up ? -d1 : d1);
         store_aff(s.maps + 36 * c, A1);
         if (fused) {
-          R z2, lnu2;
-          normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)(t + 1), 0u), &z2,
-                         &lnu2);
+          const R z2 = s.draws[2 * ((j + 1 - d0) * C + c)];
+          const R lnu2 = s.draws[2 * ((j + 1 - d0) * C + c) + 1];
           const R th2 = s.theta[(k + 1) * C + c];
           const R thn2 = propose(th2, z2, a.sigma, a.lattice_K);
           s.thn[C + c] = thn2;

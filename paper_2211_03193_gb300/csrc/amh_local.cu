@@ -37,12 +37,13 @@ __host__ __device__ inline size_t align32l(size_t x) { return (x + 31) & ~size_t
 
 template <class R>
 struct LLayout {
-  size_t theta, tr, cbs, acc, total;
+  size_t theta, draws, tr, cbs, acc, total;
   __host__ __device__ LLayout(int nmax, int Gc, int threads, int window) {
     const int h = window / 2;
     const int Lmax = nmax / 2;
     size_t o = 0;
     theta = o; o = align32l(o + sizeof(R) * (size_t)nmax * Gc);
+    draws = o; o = align32l(o + sizeof(R) * 2 * (size_t)nmax * Gc);
     tr = o;    o = align32l(o + sizeof(Pt4<R>) * 3 * (size_t)Lmax * Gc);
     cbs = o;   o = align32l(o + sizeof(R) * (size_t)(2 * h + 1) * 3 * threads);
     acc = o;   o = align32l(o + sizeof(unsigned long long) * Gc);
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
   __shared__ int s_group;
   const LLayout<R> lay(a.nmax, Gc, blockDim.x, a.window);
   R* th_s = (R*)(smem + lay.theta);          // [k][Gc]
+  R* dr_s = (R*)(smem + lay.draws);          // [k][Gc][2]: (z, ln u) of this sweep's proposals
   Pt4<R>* tr_s = (Pt4<R>*)(smem + lay.tr);   // [i][Gc][3]: T_i, i >= 1
   R* cbs = (R*)(smem + lay.cbs);             // [(j*3+xyz)][threads]
   unsigned long long* acc_s = (unsigned long long*)(smem + lay.acc);
@@ -109,6 +111,18 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
     const long long nsw = a.steps_are_sweeps ? a.steps : a.steps / n;
     __syncthreads();
     for (long long sw = 0; sw < nsw; ++sw) {
+      // the sweep's draws, all at once (they depend on the counter only):
+      // no Philox on a window's critical path
+      for (int idx = tid; idx < n * Gc; idx += nt) {
+        const int k = idx / Gc, c = idx - k * Gc;
+        R z, lnu;
+        normal_and_lnu(draw_words(a.seed, (uint32_t)(G.chain0 + c),
+                                  (unsigned long long)(t0 + sw * n + k), 0u),
+                       &z, &lnu);
+        dr_s[2 * idx] = z;
+        dr_s[2 * idx + 1] = lnu;
+      }
+      __syncthreads();
       int slot0 = 0;  // visit slot of the colour's first torsion
       for (int r = 0; r < ncol; ++r) {
         const int cnt = colour_count(n, ncol, r);
@@ -118,17 +132,16 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
           if (c >= G.nchains) continue;
           const int k = r + w * ncol;
           const int chain = G.chain0 + c;
-          const long long t = t0 + sw * n + k;
-          R z, lnu;
-          normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)t, 0u), &z,
-                         &lnu);
+          const R z = dr_s[2 * (k * Gc + c)], lnu = dr_s[2 * (k * Gc + c) + 1];
           const R th = th_s[k * Gc + c];
           const R thn = propose(th, z, a.sigma, a.lattice_K);
           const int i = k >> 1;
           const int lo = max(0, i - h), hi = min(L - 1, i + h);
           const int p = (k + 1) >> 1;
-          double dE = 0.0;
-          if (p > lo && p <= hi) {
+          typename AccT<R>::T acc = 0;
+          const bool scored = p > lo && p <= hi;
+          Aff<R> A;  // the move
+          if (scored) {
             // window coordinates: residue rr at M = T_{lo+1} o ... o T_rr
             // applied to the canonical residue; remember the bond axis
             Aff<R> M = identity_map<R>();
@@ -150,8 +163,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                 }
               }
             }
-            const Aff<R> A = rotation(Pax, Qax, wrap_angle(thn - th));
-            typename AccT<R>::T acc = 0;
+            A = rotation(Pax, Qax, wrap_angle(thn - th));
             for (int b = p; b <= hi; ++b) {
               const int jb = b - lo;
               const V3<R> xb = v3<R>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
@@ -169,14 +181,18 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                 row += L - aa - 2;
               }
             }
-            dE = (double)acc;
           }
+          const double dE = (double)acc;
           const double Tc = a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
-          const int accept = (double)lnu * Tc < -dE;  // ln u < -dE / T, T > 0
+          // ln u < -dE / T with T > 0 (FP32 form: in FP32, the precision of dE)
+          const int accept = sizeof(R) == 4 ? (float)lnu * (float)Tc < -(float)acc
+                                            : (double)lnu * Tc < -dE;
           if (accept) {
             th_s[k * Gc + c] = thn;
             atomicAdd(&acc_s[c], 1ull);
-            // T_p depends on torsions 2p-1 and 2p, one of which is k
+            // T_p depends on torsions 2p-1 and 2p, one of which is k: rebuilt
+            // from them (composing the move into T_p instead lost ~1e-6 of
+            // orthonormality per update, ~1e-3 in later Delta-E)
             if (p >= 1 && p < L)
               aff_store4(tr_s + ((size_t)p * Gc + c) * 3,
                          residue_step(a.geom, cr, th_s[(2 * p - 1) * Gc + c],
