@@ -310,6 +310,74 @@ __device__ __forceinline__ Aff<R> residue_step(const Geom<R>& g, const Canonical
   return T;
 }
 
+// T(psi, phi) = R_psi(psi) o T(0, 0) o R_phi(phi): changing psi_{i-1} turns
+// residue i rigidly about a bond fixed in residue i-1's frame, changing
+// phi_i turns residue i's frame about its own N-CA bond.  Each rotation is
+// affine in (1, cos, sin), so T is bilinear in (1, cos psi, sin psi) x
+// (1, cos phi, sin phi): T = sum_ab f_a(psi) g_b(phi) K_ab.  The nine K_ab
+// follow from T on the grid {0, pi/2, pi}^2 (K_1 = (T(0) + T(pi))/2,
+// K_cos = (T(0) - T(pi))/2, K_sin = T(pi/2) - K_1 per angle).
+// residue_basis fills kb[0..108) with the K_ab (kb[108..216) is scratch);
+// every thread of the CTA must call it.
+__device__ inline void residue_basis(const Geom<double>& g, double* kb) {
+  const double ang[3] = {0.0, 1.5707963267948966, 3.141592653589793};
+  double* S = kb + 108;  // [9][12]: T at (psi_i, phi_j)
+  if (threadIdx.x < 9) {
+    const CanonicalResidue<double> cr = canonical_residue(g);
+    const Aff<double> T = residue_step(g, cr, ang[threadIdx.x / 3], ang[threadIdx.x % 3]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) S[threadIdx.x * 12 + q] = T.m[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[threadIdx.x * 12 + 9 + q] = T.t[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    const int q = threadIdx.x;
+    double Y[3][3];  // [psi coefficient][phi sample]
+    for (int j = 0; j < 3; ++j) {
+      const double t0 = S[(0 * 3 + j) * 12 + q], t1 = S[(1 * 3 + j) * 12 + q],
+                   t2 = S[(2 * 3 + j) * 12 + q];
+      Y[0][j] = 0.5 * (t0 + t2);
+      Y[1][j] = 0.5 * (t0 - t2);
+      Y[2][j] = t1 - Y[0][j];
+    }
+    for (int a = 0; a < 3; ++a) {
+      const double k0 = 0.5 * (Y[a][0] + Y[a][2]);
+      kb[(a * 3 + 0) * 12 + q] = k0;
+      kb[(a * 3 + 1) * 12 + q] = 0.5 * (Y[a][0] - Y[a][2]);
+      kb[(a * 3 + 2) * 12 + q] = Y[a][1] - k0;
+    }
+  }
+  __syncthreads();
+}
+
+// T_i from the basis of residue_basis: two sincos and 108 FMA.
+__device__ __forceinline__ Aff<double> residue_step_basis(const double* kb, double psi,
+                                                          double phi) {
+  double sp, cp, sf, cf;
+  sincos(psi, &sp, &cp);
+  sincos(phi, &sf, &cf);
+  const double f[3] = {1.0, cp, sp}, gg[3] = {1.0, cf, sf};
+  double v[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) v[q] = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const double w = f[a] * gg[b];
+      const double* K = kb + (a * 3 + b) * 12;
+#pragma unroll
+      for (int q = 0; q < 12; ++q) v[q] = fma(w, K[q], v[q]);
+    }
+  Aff<double> T;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) T.m[q] = v[q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) T.t[q] = v[9 + q];
+  return T;
+}
+
 __device__ __forceinline__ Aff<double> shfl_up_aff(const Aff<double>& A, int off, int width) {
   Aff<double> B;
 #pragma unroll
@@ -320,7 +388,7 @@ __device__ __forceinline__ Aff<double> shfl_up_aff(const Aff<double>& A, int off
 }
 
 // Build G(s) of `nch` chains with the first nthreads threads of the CTA
-// (0: all): chain c uses the tpc = nthreads / nslots consecutive threads
+// (0: all), kb the basis of residue_basis: chain c uses the tpc = nthreads / nslots consecutive threads
 // starting at c * tpc (tpc a power of two).  theta(c, k) reads torsion k of
 // chain c; emit(c, i, N, CA, C, CB) stores residue i.  scratch: nslots *
 // max(tpc/32, 1) * 12 doubles of shared memory.  cache (optional, nslots * L
@@ -328,8 +396,9 @@ __device__ __forceinline__ Aff<double> shfl_up_aff(const Aff<double>& A, int off
 // recompute it.  Must be called by every one of those threads; with tpc > 32
 // it synchronises the whole CTA, so then nthreads must be the CTA.
 template <class TH, class EMIT>
-__device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH theta, EMIT emit,
-                                  double* scratch, double* cache = nullptr, int nthreads = 0) {
+__device__ void build_chains_scan(const Geom<double>& g, const double* kb, int L, int nslots,
+                                  TH theta, EMIT emit, double* scratch, double* cache = nullptr,
+                                  int nthreads = 0) {
   const int tpc = (nthreads ? nthreads : (int)blockDim.x) / nslots;
   const int c = threadIdx.x / tpc, r = threadIdx.x % tpc;
   const int width = tpc < 32 ? tpc : 32;
@@ -341,7 +410,7 @@ __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH t
   const int r0 = min(L, r * nb), r1 = min(L, r0 + nb);
   Aff<double> agg = identity_map<double>();
   for (int i = max(r0, 1); i < r1; ++i) {
-    const Aff<double> T = residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i));
+    const Aff<double> T = residue_step_basis(kb, theta(c, 2 * i - 1), theta(c, 2 * i));
     if (cache) {
       double* q = cache + ((size_t)c * L + i) * 12;
 #pragma unroll
@@ -391,7 +460,7 @@ __device__ void build_chains_scan(const Geom<double>& g, int L, int nslots, TH t
 #pragma unroll
         for (int k = 0; k < 3; ++k) T.t[k] = q[9 + k];
       } else {
-        T = residue_step(g, cr, theta(c, 2 * i - 1), theta(c, 2 * i));
+        T = residue_step_basis(kb, theta(c, 2 * i - 1), theta(c, 2 * i));
       }
       P = compose(P, T);
     }

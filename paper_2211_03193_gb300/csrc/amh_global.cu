@@ -38,7 +38,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 31) & ~size_t(
 // Dynamic shared memory layout of a global-sweep CTA.
 template <class R, int C>
 struct Layout {
-  size_t theta, bb, cb, draws, maps, list, fsph, bits, part, partf, ecur, thn, lnu, acc, commit, flag, scan,
+  size_t theta, bb, cb, draws, kb, maps, list, fsph, bits, part, partf, ecur, thn, lnu, acc, commit, flag, scan,
       bars, ring, total;
   int ls;  // stride between chains of the C-beta array (odd: conflict-free 16-byte loads)
   int nm;  // moving atoms at most: stride of the chunk bits per chain
@@ -56,6 +56,7 @@ struct Layout {
     ls = Lmax | 1;
     cb = o;    o = align16(o + sizeof(Pt4<R>) * (size_t)ls * C);
     draws = o; o = align16(o + sizeof(R) * 2 * kDraw * C);
+    kb = o;    o = align16(o + sizeof(double) * 216);
     maps = o;  o = align16(o + sizeof(R) * 36 * C);
     list = o;  o = align16(o + (far ? sizeof(unsigned short) * (size_t)nM * nJ : 0));
     fsph = o;  o = align16(o + (far ? sizeof(Pt4<R>) * (size_t)nJ * C : 0));
@@ -82,6 +83,7 @@ struct Shm {
   R* bb;     // [((i*3+atom)*3+xyz)][C], atom 0 N, 1 CA, 2 C
   Pt4<R>* cb4;  // [C][ls]: chain-major, odd stride
   R* draws;     // [kDraw][C][2]: (z, ln u) of the next proposals
+  double* kb;   // residue-transform basis (residue_basis), 216 doubles
   R* maps;   // [C][36]: A1, A2, A21
   unsigned short* list;  // items kept by the far-field test, in order
   Pt4<R>* fsph;    // [chunk][C]: centre and radius of a fixed-side chunk's C-betas
@@ -103,6 +105,7 @@ struct Shm {
     bb = (R*)(base + l.bb);
     cb4 = (Pt4<R>*)(base + l.cb);
     draws = (R*)(base + l.draws);
+    kb = (double*)(base + l.kb);
     maps = (R*)(base + l.maps);
     list = (unsigned short*)(base + l.list);
     fsph = (Pt4<R>*)(base + l.fsph);
@@ -157,7 +160,7 @@ __device__ __forceinline__ V3<R> to_r(V3<double> v) {
 template <class R, int C>
 __device__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
   build_chains_scan(
-      g, L, C, [&](int c, int k) { return (double)s.theta[k * C + c]; },
+      g, s.kb, L, C, [&](int c, int k) { return (double)s.theta[k * C + c]; },
       [&](int c, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
         s.set_atom(i, 0, c, to_r<R>(N));
         s.set_atom(i, 1, c, to_r<R>(CA));
@@ -931,6 +934,7 @@ __global__ void __launch_bounds__(512) global_kernel(SweepArgs<R> a) {
     mbar_init_fence();
   }
   unsigned par = 0;  // per warp: phase parity to wait for, one bit per slot
+  residue_basis(a.geom64, s.kb);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_group = s_abort ? a.ngroups : atomicAdd(a.queue, 1);
@@ -949,6 +953,7 @@ __global__ void __launch_bounds__(512) energy_kernel(SweepArgs<R> a) {
   __shared__ int s_group;
   const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);
   Shm<R, C> s(smem, lay);
+  residue_basis(a.geom64, s.kb);
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_group = atomicAdd(a.queue, 1);

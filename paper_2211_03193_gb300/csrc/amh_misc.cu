@@ -13,7 +13,7 @@ constexpr int kGradParts = 4;
 
 size_t grad_smem_bytes(size_t rsize, int L) {
   return ((rsize * (12 + 3 * kGradParts) * L + 15) & ~(size_t)15) + sizeof(double) * 6 * (L + 1) +
-         sizeof(double) * 12 * 8;
+         sizeof(double) * (12 * 8 + 216);
 }
 
 // The residue-transform cache (12 doubles per residue) is used when it fits.
@@ -99,15 +99,17 @@ __global__ void __launch_bounds__(kGradThreads) grad_kernel(int L, long long tab
   double* GM = (double*)(smem + (((size_t)sizeof(R) * (12 + 3 * kGradParts) * L + 15) &
                                  ~(size_t)15));  // [L+1][6]
   double* scan = GM + (size_t)6 * (L + 1);  // [8][12] warp totals of the chain-building scan
-  double* cache = scan + 8 * 12;            // [L][12] residue transforms (if use_cache)
+  double* kb = scan + 8 * 12;               // [216] residue-transform basis
+  double* cache = kb + 216;                 // [L][12] residue transforms (if use_cache)
   __shared__ double wpart[64];  // warp energy partials, then the suffix scan's 8 x 6 totals
   const int v = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const R* th = theta + (size_t)v * n;
   // G(s) built in FP64 by one warp (FP64 is the scarce pipe: a wider scan
   // composes more transforms in all), stored in R as the sweeps' resync does
+  residue_basis(geom, kb);
   if (tid < 32)
     build_chains_scan(
-        geom, L, 1, [&](int, int k) { return (double)th[k]; },
+        geom, kb, L, 1, [&](int, int k) { return (double)th[k]; },
         [&](int, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
           const V3<double> at[4] = {N, CA, Cc, CB};
 #pragma unroll
