@@ -362,6 +362,31 @@ __device__ __forceinline__ Pt4<float> pt4of(V3<float> v) {
   return p;
 }
 
+// Bounding spheres (box centre, largest distance) of the fixed side's
+// kFC-atom chunks, one thread per (chunk, chain) among threads [t0, t0 + nt).
+// They do not depend on the proposal, so warps other than the one drawing
+// and rotating compute them meanwhile.
+template <int C>
+__device__ void far_spheres(Shm<float, C>& s, int f0, int f1, int t0, int nt) {
+  const int nJ = (f1 - f0 + kFC - 1) / kFC;
+  for (int t = (int)threadIdx.x - t0; t < nJ * C; t += nt) {
+    const int j = t / C, c = t - j * C;
+    const int fb = f0 + kFC * j, fe = min(fb + kFC, f1);
+    V3<float> lo = s.cb(fb, c), hi = lo;
+    for (int f = fb + 1; f < fe; ++f) {
+      const V3<float> x = s.cb(f, c);
+      lo = v3<float>(fminf(lo.x, x.x), fminf(lo.y, x.y), fminf(lo.z, x.z));
+      hi = v3<float>(fmaxf(hi.x, x.x), fmaxf(hi.y, x.y), fmaxf(hi.z, x.z));
+    }
+    const V3<float> o = (lo + hi) * 0.5f;
+    float r2 = 0.f;
+    for (int f = fb; f < fe; ++f) r2 = fmaxf(r2, dist2(s.cb(f, c), o));
+    Pt4<float> q = pt4of(o);
+    q.w = sqrtf(r2);
+    s.fsph[j * C + c] = q;
+  }
+}
+
 // The straddle block without its flat far field (FP32).  Beyond the last
 // bin centre the Eq. 5 term is the constant -ln p of the last bin, so a pair
 // whose distance is past it before and after the move adds exactly zero to
@@ -378,25 +403,6 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int nM = m1 - m0, nJ = (f1 - f0 + kFC - 1) / kFC;
   const int nMs = s.nm;  // stride of s.bits per chain
-  // (1) one thread per (chunk, chain): the bounding box's centre and the
-  // largest distance from it
-  for (int t = threadIdx.x; t < nJ * C; t += blockDim.x) {
-    const int j = t / C, c = t - j * C;
-    const int fb = f0 + kFC * j, fe = min(fb + kFC, f1);
-    V3<float> lo = s.cb(fb, c), hi = lo;
-    for (int f = fb + 1; f < fe; ++f) {
-      const V3<float> x = s.cb(f, c);
-      lo = v3<float>(fminf(lo.x, x.x), fminf(lo.y, x.y), fminf(lo.z, x.z));
-      hi = v3<float>(fmaxf(hi.x, x.x), fmaxf(hi.y, x.y), fmaxf(hi.z, x.z));
-    }
-    const V3<float> o = (lo + hi) * 0.5f;
-    float r2 = 0.f;
-    for (int f = fb; f < fe; ++f) r2 = fmaxf(r2, dist2(s.cb(f, c), o));
-    Pt4<float> q = pt4of(o);
-    q.w = sqrtf(r2);
-    s.fsph[j * C + c] = q;
-  }
-  __syncthreads();
   // (2) one thread per (moving atom, chain): the images' sphere and the
   // chunks within reach, as bits
   for (int t = threadIdx.x; t < nM * C; t += blockDim.x) {
@@ -750,6 +756,11 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     const int m0 = up ? 0 : p, m1 = up ? p : L;
     const int f0 = up ? p : 0, f1 = up ? L : p;
     const bool dead = (k == 0) || (k == n - 1);
+    if constexpr (sizeof(R) == 4 && !ST) {
+      // the far-field test's chunk spheres, by the warps that do not draw
+      if (a.far_skip && !dead && threadIdx.x >= 32)
+        far_spheres<C>(s, f0, f1, 32, (int)blockDim.x - 32);
+    }
     if (threadIdx.x < C) {
       const int c = threadIdx.x;
       const int chain = G.chain0 + c;
