@@ -67,6 +67,9 @@ def _init(lib, **over):
     dict(opt=dict(precision=16)),
     dict(opt=dict(chains_per_cta=3)),
     dict(opt=dict(threads_per_cta=96)),
+    dict(opt=dict(far_pairs=2)),
+    dict(opt=dict(table_texture=3)),
+    dict(opt=dict(stage_table=-1)),
 ])
 def test_bad_arguments_are_refused_before_any_device_work(lib, over):
     st, h = _init(lib, **over)
@@ -78,7 +81,15 @@ def test_bad_arguments_are_refused_before_any_device_work(lib, over):
 def test_null_context_calls_return_estate(lib):
     assert lib.amh_energy(None, None) == 5
     assert lib.amh_sweep(None, 1, 0, 1.0, 0.1, 10, 1, None) == 5
+    v = ctypes.c_ulonglong()
+    assert lib.amh_pair_terms(None, ctypes.byref(v)) == 5
     lib.amh_destroy(None)
+
+
+def test_options_default_far_field_skip_on():
+    from paper_2211_03193_gb300 import _amh
+    o = _amh.amh_options_default()
+    assert o.far_pairs == 0 and o.table_texture == 0 and o.threads_per_cta == 0
 
 
 def test_peaks_library_exports_its_symbol():
