@@ -451,6 +451,16 @@ def run_grad():
             e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
+        # the L-BFGS hand-off's call: 32 vectors, one call at a time
+        th32 = th[:32].contiguous()
+        E32 = torch.empty(32, dtype=torch.float64, device="cuda")
+        G32 = torch.empty((32, n), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t32 = time.perf_counter()
+        for _ in range(50):
+            s.grad(0, th32, E32, G32)
+            torch.cuda.synchronize()
+        ms32 = (time.perf_counter() - t32) / 50 * 1000.0
     chains = 256
     starts = synth.random_torsions(chains, L, seed=w["start_seed"] + 1)
     with Sampler(prot, chains, starts) as s:
@@ -460,15 +470,24 @@ def run_grad():
         th_all, E0, _, _ = s.state()
         best = np.argsort(E0)[:32]
         t1 = time.perf_counter()
+        calls = [0]
+        plain_grad = s.grad
+
+        def counted(*a, **k):
+            calls[0] += 1
+            return plain_grad(*a, **k)
+        s.grad = counted
         thL, EL = autograd.lbfgs_refine(s, torch.tensor(th_all.reshape(chains, n)[best],
                                                         device="cuda"), iterations=500)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         EL = EL.cpu().numpy()
     print(json.dumps({"experiment": "grad", "L": L, "batch": batch, "ms_per_call": ms,
+                      "ms_per_call_32_synchronised": ms32,
                       "vectors_per_s": batch / (ms / 1000.0),
                       "pair_gradients_per_s": batch * L * (L - 1) / (ms / 1000.0),
                       "amh_seconds": t1 - t0, "lbfgs_seconds": t2 - t1,
+                      "lbfgs_gradient_calls": calls[0],
                       "best32_energy_before": [float(E0[best].min()), float(E0[best].max())],
                       "best32_energy_after": [float(EL.min()), float(EL.max())]}))
 
