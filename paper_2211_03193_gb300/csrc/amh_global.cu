@@ -369,21 +369,25 @@ __device__ __forceinline__ Pt4<float> pt4of(V3<float> v) {
 template <int C>
 __device__ void far_spheres(Shm<float, C>& s, int f0, int f1, int t0, int nt) {
   const int nJ = (f1 - f0 + kFC - 1) / kFC;
+  const Pt4<float>* __restrict__ cb4 = s.cb4;  // kept in registers for the loops
+  Pt4<float>* __restrict__ fsph = s.fsph;
+  const int ls = s.ls;
   for (int t = (int)threadIdx.x - t0; t < nJ * C; t += nt) {
     const int j = t / C, c = t - j * C;
     const int fb = f0 + kFC * j, fe = min(fb + kFC, f1);
-    V3<float> lo = s.cb(fb, c), hi = lo;
+    const Pt4<float>* x = cb4 + c * ls;
+    V3<float> lo = v3of(x[fb]), hi = lo;
     for (int f = fb + 1; f < fe; ++f) {
-      const V3<float> x = s.cb(f, c);
-      lo = v3<float>(fminf(lo.x, x.x), fminf(lo.y, x.y), fminf(lo.z, x.z));
-      hi = v3<float>(fmaxf(hi.x, x.x), fmaxf(hi.y, x.y), fmaxf(hi.z, x.z));
+      const Pt4<float> y = x[f];
+      lo = v3<float>(fminf(lo.x, y.x), fminf(lo.y, y.y), fminf(lo.z, y.z));
+      hi = v3<float>(fmaxf(hi.x, y.x), fmaxf(hi.y, y.y), fmaxf(hi.z, y.z));
     }
     const V3<float> o = (lo + hi) * 0.5f;
     float r2 = 0.f;
-    for (int f = fb; f < fe; ++f) r2 = fmaxf(r2, dist2(s.cb(f, c), o));
+    for (int f = fb; f < fe; ++f) r2 = fmaxf(r2, dist2(v3of(x[f]), o));
     Pt4<float> q = pt4of(o);
     q.w = sqrtf(r2);
-    s.fsph[j * C + c] = q;
+    fsph[j * C + c] = q;
   }
 }
 
@@ -403,6 +407,8 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int nM = m1 - m0, nJ = (f1 - f0 + kFC - 1) / kFC;
   const int nMs = s.nm;  // stride of s.bits per chain
+  const Pt4<float>* __restrict__ fsph = s.fsph;
+  ChunkBits* __restrict__ bits = s.bits;
   // (2) one thread per (moving atom, chain): the images' sphere and the
   // chunks within reach, as bits
   for (int t = threadIdx.x; t < nM * C; t += blockDim.x) {
@@ -428,12 +434,12 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
       }
       const float reach = sqrtf(r2) + cut;
       for (int j = 0; j < nJ; ++j) {
-        const Pt4<float> q = s.fsph[j * C + c];
+        const Pt4<float> q = fsph[j * C + c];
         const float lim = reach + q.w;
         if (dist2(o, v3of(q)) < lim * lim) b |= ChunkBits(1) << j;
       }
     }
-    s.bits[c * nMs + mi] = b;
+    bits[c * nMs + mi] = b;
   }
   __syncthreads();
   // (3) the items kept for any chain, in item order (a block-wide scan of
@@ -441,7 +447,7 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   auto kept = [&](int mi) {
     ChunkBits w = 0;
 #pragma unroll
-    for (int c = 0; c < C; ++c) w |= s.bits[c * nMs + mi];
+    for (int c = 0; c < C; ++c) w |= bits[c * nMs + mi];
     return w;
   };
   const int per = (nM + blockDim.x - 1) / blockDim.x;

@@ -207,16 +207,19 @@ def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads, te
         assert np.all(bE <= E + 1e-9)
 
 
-@pytest.mark.parametrize("C", [8, 2])
-def test_far_field_skip_equals_dense(amh, orc, C):
+@pytest.mark.parametrize("C,wide", [(8, False), (2, False), (4, True)])
+def test_far_field_skip_equals_dense(amh, orc, C, wide):
     """FP32 global sweeps with the flat far field skipped (the default) and
     with every straddle pair evaluated, from the same states and seeds: the
     same Delta-E within FP32 rounding of the different summation order, the
     same decisions up to the first near-tie, and oracle parity (teacher-forced
-    replay) for the skipping run.  L=150 from random starts, so most
-    (moving atom, chunk) items are far."""
+    replay) for the skipping run.  L=150 from random starts: with the 37
+    bins up to 20 A most (moving atom, chunk) items are far; with 64 bins up
+    to 66 A most are kept."""
     L, chains = 150, 16
-    prot = synth.make_protein(L, seed=305)
+    edges = np.linspace(2.0, 66.0, 65) if wide else None
+    prot = (synth.make_protein(L, edges=edges, sigma_d=2.0, seed=305) if wide
+            else synth.make_protein(L, seed=305))
     tors = synth.random_torsions(chains, L, seed=306)
     n = 2 * L
     steps = n + 3
