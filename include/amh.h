@@ -69,7 +69,9 @@ typedef struct {
   int table_is_neglog;     /* 0: table holds p; 1: table already holds -ln p */
   int stage_table;         /* global sweeps read the straddle block's table rows
                               0: as tuned (staged in shared memory by bulk
-                              async copies when it fits), 1: always staged
+                              async copies when the autotuner finds it faster;
+                              with a fixed chains_per_cta, staged when it fits
+                              and the far-field skip is off), 1: always staged
                               (AMH_EINVAL if impossible: needs precision 32
                               and 4 or 8 chains per CTA), 2: never staged
                               (read through the L1 cache). */
@@ -81,7 +83,7 @@ typedef struct {
   int far_pairs;           /* precision 32, global sweeps: 0 = skip the straddle
                               pairs that stay beyond the last bin centre before
                               and after the move (their Eq. 5 terms are equal,
-                              so Delta V is unchanged; found per 32-atom chunk
+                              so Delta V is unchanged; found per 12-atom chunk
                               of the fixed side by bounding spheres) (default);
                               1 = evaluate every straddle pair. */
   void* stream;            /* cudaStream_t; NULL = the legacy default stream */

@@ -491,7 +491,13 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   } else {
     const int C = ctx->opt.chains_per_cta;
     const int T = ctx->opt.threads_per_cta ? ctx->opt.threads_per_cta : 256;
-    const int D = ctx->opt.stage_table == 2 ? 0 : stage_depth_for(ctx, C, T);
+    // staged rows run every straddle pair: with the far-field skip on, a
+    // fixed shape stages only when asked to
+    const bool skip = ctx->precision == 32 && ctx->opt.far_pairs == 0 &&
+                      ctx->Lmax <= kMaxChunks * kPairChunk + 1;
+    const int D = ctx->opt.stage_table == 2 || (ctx->opt.stage_table == 0 && skip)
+                      ? 0
+                      : stage_depth_for(ctx, C, T);
     if (ctx->opt.stage_table == 1 && D == 0)
       return set_err(ctx, AMH_EINVAL, "table staging needs FP32, 4 or 8 chains per CTA and room");
     st = configure_global<R>(ctx, C, T, D);

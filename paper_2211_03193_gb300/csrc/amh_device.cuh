@@ -172,12 +172,11 @@ __device__ __forceinline__ V3<R> apply(const Aff<R>& A, V3<R> x) {
                fma(A.m[6], x.x, fma(A.m[7], x.y, fma(A.m[8], x.z, A.t[2]))));
 }
 
-// Right-handed rotation by angle `ang` about the axis through P towards Q.
-// Raising a dihedral by delta turns the far-side atoms by +delta about the
-// bond from its second to its third atom.
+// Right-handed rotation by angle `ang` about the line through P along the
+// unit vector u.  Raising a dihedral by delta turns the far-side atoms by
+// +delta about the bond from its second to its third atom.
 template <class R>
-__device__ __forceinline__ Aff<R> rotation(V3<R> P, V3<R> Q, R ang) {
-  V3<R> u = unit(Q - P);
+__device__ __forceinline__ Aff<R> rotation_axis(V3<R> P, V3<R> u, R ang) {
   R s, c;
   sincos_(ang, &s, &c);
   R oc = R(1) - c;
@@ -196,6 +195,20 @@ __device__ __forceinline__ Aff<R> rotation(V3<R> P, V3<R> Q, R ang) {
   A.t[1] = P.y - (A.m[3] * P.x + A.m[4] * P.y + A.m[5] * P.z);
   A.t[2] = P.z - (A.m[6] * P.x + A.m[7] * P.y + A.m[8] * P.z);
   return A;
+}
+
+// The same about the axis through P towards Q.
+template <class R>
+__device__ __forceinline__ Aff<R> rotation(V3<R> P, V3<R> Q, R ang) {
+  return rotation_axis(P, unit(Q - P), ang);
+}
+
+// The linear part of A applied to a direction.
+template <class R>
+__device__ __forceinline__ V3<R> lin(const Aff<R>& A, V3<R> v) {
+  return v3<R>(fma(A.m[0], v.x, fma(A.m[1], v.y, A.m[2] * v.z)),
+               fma(A.m[3], v.x, fma(A.m[4], v.y, A.m[5] * v.z)),
+               fma(A.m[6], v.x, fma(A.m[7], v.y, A.m[8] * v.z)));
 }
 
 // B o A (apply A first).

@@ -80,11 +80,11 @@ struct Layout {
 template <class R, int C>
 struct Shm {
   R* theta;  // [k][C]
-  R* bb;     // [((i*3+atom)*3+xyz)][C], atom 0 N, 1 CA, 2 C
+  R* bb;     // [((i*3+v)*3+xyz)][C]: v 0 CA_i, 1 unit N_i -> CA_i, 2 unit CA_i -> C_i
   Pt4<R>* cb4;  // [C][ls]: chain-major, odd stride
   R* draws;     // [kDraw][C][2]: (z, ln u) of the next proposals
   double* kb;   // residue-transform basis (residue_basis), 216 doubles
-  R* maps;   // [C][36]: A1, A2, A21
+  R* maps;   // [C][36]: moves A1, A2, A21 (see load_rot)
   unsigned short* list;  // items kept by the far-field test, in order
   Pt4<R>* fsph;    // [chunk][C]: centre and radius of a fixed-side chunk's C-betas
   ChunkBits* bits;  // [C][moving atom]: chunks whose pairs may not be flat
@@ -136,15 +136,17 @@ struct Shm {
     p.w = (R)0;
     cb4[c * ls + i] = p;
   }
-  __device__ V3<R> atom(int i, int a, int c) const {
-    const R* p = bb + (size_t)((i * 3 + a) * 3) * C + c;
+  // the torsion axes of residue i: both pass through CA_i; phi_i runs
+  // along N_i -> CA_i, psi_i along CA_i -> C_i
+  __device__ V3<R> bbv(int i, int v, int c) const {
+    const R* p = bb + (size_t)((i * 3 + v) * 3) * C + c;
     return v3<R>(p[0], p[C], p[2 * C]);
   }
-  __device__ void set_atom(int i, int a, int c, V3<R> v) {
-    R* p = bb + (size_t)((i * 3 + a) * 3) * C + c;
-    p[0] = v.x;
-    p[C] = v.y;
-    p[2 * C] = v.z;
+  __device__ void set_bbv(int i, int v, int c, V3<R> x) {
+    R* p = bb + (size_t)((i * 3 + v) * 3) * C + c;
+    p[0] = x.x;
+    p[C] = x.y;
+    p[2 * C] = x.z;
   }
 };
 
@@ -156,15 +158,18 @@ __device__ __forceinline__ V3<R> to_r(V3<double> v) {
 // G(s) of all C chain slots, built in FP64 by all threads (a parallel scan
 // of residue transforms) and stored in R: rounding the torsions' sines and
 // cosines in single precision would random-walk the frame along the chain
-// (~1e-4 A at L=300).
+// (~1e-4 A at L=300).  The torsion axes are kept as CA and two unit bond
+// directions formed in FP64: a direction from two FP32 atoms 1.46 A apart
+// would be off by up to ulp(|x|) / 1.46 A (2.6e-6 rad at 50 A), and a move
+// would carry its whole side off by that angle times the move's angle.
 template <class R, int C>
 __device__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
   build_chains_scan(
       g, s.kb, L, C, [&](int c, int k) { return (double)s.theta[k * C + c]; },
       [&](int c, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
-        s.set_atom(i, 0, c, to_r<R>(N));
-        s.set_atom(i, 1, c, to_r<R>(CA));
-        s.set_atom(i, 2, c, to_r<R>(Cc));
+        s.set_bbv(i, 0, c, to_r<R>(CA));
+        s.set_bbv(i, 1, c, to_r<R>(unit(CA - N)));
+        s.set_bbv(i, 2, c, to_r<R>(unit(Cc - CA)));
         s.set_cb(i, c, to_r<R>(CB));
       },
       s.scan);
@@ -240,31 +245,108 @@ __device__ void full_energy(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, i
   __syncthreads();
 }
 
+// Coordinates from the torsions in FP64 (G(s) of Sec. 2.1), rounded to R.
 template <class R, int C>
-__device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P) {
+__device__ void rebuild(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P) {
   __syncthreads();
   build_chains(s, a.geom64, P.L);
   __syncthreads();
+}
+
+template <class R, int C>
+__device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P) {
+  rebuild(s, a, P);
   full_energy(s, a.tab, P.tab_off, P.L);
 }
 
-// A map is 12 values at a 4-value boundary of the maps region: three
-// vector loads.
-template <class R, int C>
-__device__ __forceinline__ void load_aff(const R* src, Aff<R>& A) {
-  const Pt4<R>* q = reinterpret_cast<const Pt4<R>*>(src);
-  const Pt4<R> a = q[0], b = q[1], d = q[2];
-  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
-  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
-  A.m[8] = d.x; A.t[0] = d.y; A.t[1] = d.z; A.t[2] = d.w;
+// A proposal's rigid move, y = q + M (x - p): M a rotation, p a point and
+// q its image.  Kept this way the FP32 rounding of p and q is that of one
+// stored coordinate near the moving atoms.  The affine form x -> M x + t has
+// t = p - M p rounded at the size of the coordinates (~1e-5 A at 50-80 A
+// from the origin), one shift shared by the whole moving side, and Delta-E
+// feels it with the net force on that side (~2e4 per A: up to ~0.2 for
+// one move at L=150).
+template <class R>
+struct Move {
+  R m[9];
+  R p[3];
+  R q[3];
+};
+
+// Rotation by `ang` about the line through P along the unit vector u
+// (right-handed; see rotation_axis).
+template <class R>
+__device__ __forceinline__ Move<R> move_rotation(V3<R> P, V3<R> u, R ang) {
+  const Aff<R> A = rotation_axis(P, u, ang);
+  Move<R> M;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) M.m[i] = A.m[i];
+  M.p[0] = M.q[0] = P.x;
+  M.p[1] = M.q[1] = P.y;
+  M.p[2] = M.q[2] = P.z;
+  return M;
 }
 
 template <class R>
-__device__ __forceinline__ void store_aff(R* dst, const Aff<R>& A) {
+__device__ __forceinline__ V3<R> move_lin(const Move<R>& A, V3<R> v) {
+  return v3<R>(fma(A.m[0], v.x, fma(A.m[1], v.y, A.m[2] * v.z)),
+               fma(A.m[3], v.x, fma(A.m[4], v.y, A.m[5] * v.z)),
+               fma(A.m[6], v.x, fma(A.m[7], v.y, A.m[8] * v.z)));
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> move_apply(const Move<R>& A, V3<R> x) {
+  const R dx = x.x - A.p[0], dy = x.y - A.p[1], dz = x.z - A.p[2];
+  return v3<R>(fma(A.m[0], dx, fma(A.m[1], dy, fma(A.m[2], dz, A.q[0]))),
+               fma(A.m[3], dx, fma(A.m[4], dy, fma(A.m[5], dz, A.q[1]))),
+               fma(A.m[6], dx, fma(A.m[7], dy, fma(A.m[8], dz, A.q[2]))));
+}
+
+// B o A (apply A first): taken about A's point, which lands on B(A(p)).
+template <class R>
+__device__ __forceinline__ Move<R> move_compose(const Move<R>& B, const Move<R>& A) {
+  Move<R> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      r.m[3 * i + j] = B.m[3 * i] * A.m[j] + B.m[3 * i + 1] * A.m[3 + j] + B.m[3 * i + 2] * A.m[6 + j];
+  const V3<R> q = move_apply(B, v3<R>(A.q[0], A.q[1], A.q[2]));
+  r.p[0] = A.p[0]; r.p[1] = A.p[1]; r.p[2] = A.p[2];
+  r.q[0] = q.x; r.q[1] = q.y; r.q[2] = q.z;
+  return r;
+}
+
+// The maps region holds per chain A1, A2 and A21 as 12 values each at a
+// 4-value boundary (three vector loads): the rotations' M and p (their q is
+// p), and for A21 its M and q; its p is A1's (move 1's axis point).
+template <class R, int C>
+__device__ __forceinline__ void load_rot(const R* src, Move<R>& A) {
+  const Pt4<R>* v = reinterpret_cast<const Pt4<R>*>(src);
+  const Pt4<R> a = v[0], b = v[1], d = v[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.p[0] = A.q[0] = d.y; A.p[1] = A.q[1] = d.z; A.p[2] = A.q[2] = d.w;
+}
+
+// A21 from its 12 values and A1's point p1.
+template <class R, int C>
+__device__ __forceinline__ void load_move21(const R* src, const R* p1, Move<R>& A) {
+  const Pt4<R>* v = reinterpret_cast<const Pt4<R>*>(src);
+  const Pt4<R> a = v[0], b = v[1], d = v[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.q[0] = d.y; A.q[1] = d.z; A.q[2] = d.w;
+  A.p[0] = p1[0]; A.p[1] = p1[1]; A.p[2] = p1[2];
+}
+
+// The 12 values of a rotation (pt = p) or of A21 (pt = q).
+template <class R>
+__device__ __forceinline__ void store_move(R* dst, const Move<R>& A, const R* pt) {
 #pragma unroll
   for (int i = 0; i < 9; ++i) dst[i] = A.m[i];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) dst[9 + i] = A.t[i];
+  for (int i = 0; i < 3; ++i) dst[9 + i] = pt[i];
 }
 
 // Straddle-block Delta-E (moving side [m0, m1), fixed side [f0, f1)).
@@ -289,15 +371,15 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     const V3<R> xm = s.cb(m, c);
     // the maps are read per item (only the moved positions stay live in the
     // pair loop, leaving registers for more loads in flight)
-    Aff<R> A;
-    load_aff<R, C>(s.maps + 36 * c, A);
-    const V3<R> y1 = apply(A, xm);
+    Move<R> A;
+    load_rot<R, C>(s.maps + 36 * c, A);
+    const V3<R> y1 = move_apply(A, xm);
     V3<R> y2, y21;
     if (FUSED) {
-      load_aff<R, C>(s.maps + 36 * c + 12, A);
-      y2 = apply(A, xm);
-      load_aff<R, C>(s.maps + 36 * c + 24, A);
-      y21 = apply(A, xm);
+      load_move21<R, C>(s.maps + 36 * c + 24, A.p, A);
+      y21 = move_apply(A, xm);
+      load_rot<R, C>(s.maps + 36 * c + 12, A);
+      y2 = move_apply(A, xm);
     }
     const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
     // rows of the pairs (f, m): contiguous in f when m < f; when f < m,
@@ -343,11 +425,6 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     reduce3(s, (double)acc1, (double)acc2, (double)acc21);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 __device__ __forceinline__ float dist2(V3<float> a, V3<float> b) {
   const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -416,16 +493,16 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
     ChunkBits b = 0;
     if ((real >> c) & 1u) {
       const V3<float> xm = s.cb(m0 + mi, c);
-      Aff<float> A;
-      load_aff<float, C>(s.maps + 36 * c, A);
-      const V3<float> y1 = apply(A, xm);
+      Move<float> A;
+      load_rot<float, C>(s.maps + 36 * c, A);
+      const V3<float> y1 = move_apply(A, xm);
       V3<float> o;
       float r2;
       if (FUSED) {
-        load_aff<float, C>(s.maps + 36 * c + 12, A);
-        const V3<float> y2 = apply(A, xm);
-        load_aff<float, C>(s.maps + 36 * c + 24, A);
-        const V3<float> y21 = apply(A, xm);
+        load_move21<float, C>(s.maps + 36 * c + 24, A.p, A);
+        const V3<float> y21 = move_apply(A, xm);
+        load_rot<float, C>(s.maps + 36 * c + 12, A);
+        const V3<float> y2 = move_apply(A, xm);
         o = (xm + y1 + y2 + y21) * 0.25f;
         r2 = fmaxf(fmaxf(dist2(xm, o), dist2(y1, o)), fmaxf(dist2(y2, o), dist2(y21, o)));
       } else {
@@ -530,11 +607,11 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
   const int Bp = tb.Bp;
   const int RB = Bp * (int)sizeof(float2);
   const float2* tab = tb.E + tab_off;
-  Aff<float> A1, A2, A21;
-  load_aff<float, C>(s.maps + 36 * c, A1);
+  Move<float> A1, A2, A21;
+  load_rot<float, C>(s.maps + 36 * c, A1);
   if (FUSED) {
-    load_aff<float, C>(s.maps + 36 * c + 12, A2);
-    load_aff<float, C>(s.maps + 36 * c + 24, A21);
+    load_rot<float, C>(s.maps + 36 * c + 12, A2);
+    load_move21<float, C>(s.maps + 36 * c + 24, A1.p, A21);
   }
   const int nF = f1 - f0;
   const int nch = (nF + kFC - 1) / kFC;
@@ -578,10 +655,10 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
     V3<float> xm = v3<float>(0.f, 0.f, 0.f), y1 = xm, y2 = xm, y21 = xm;
     if (act) {
       xm = s.cb(m, c);
-      y1 = apply(A1, xm);
+      y1 = move_apply(A1, xm);
       if (FUSED) {
-        y2 = apply(A2, xm);
-        y21 = apply(A21, xm);
+        y2 = move_apply(A2, xm);
+        y21 = move_apply(A21, xm);
       }
     }
     const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
@@ -629,8 +706,8 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
 template <class R, int C>
 __device__ void commit_moves(Shm<R, C>& s, int m0, int m1, bool cb_only) {
   // cb_only: the upstream side moved; the rest of this sweep rotates about
-  // bonds at or after the pivot and never reads these residues' backbone
-  // atoms (a new sweep starts from a rebuild), so only the C-betas move
+  // bonds at or after the pivot and never reads these residues' torsion
+  // axes (a new sweep starts from a rebuild), so only the C-betas move
   const int per = cb_only ? 1 : 4;
   const int total = (m1 - m0) * per * C;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -638,13 +715,18 @@ __device__ void commit_moves(Shm<R, C>& s, int m0, int m1, bool cb_only) {
     const int code = s.commit[c];
     if (!code) continue;
     const int rest = idx / C;
-    const int atom = cb_only ? 3 : rest & 3, i = m0 + (cb_only ? rest : rest >> 2);
-    Aff<R> A;
-    load_aff<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
-    if (atom < 3) {
-      s.set_atom(i, atom, c, apply(A, s.atom(i, atom, c)));
+    const int v = cb_only ? 3 : rest & 3, i = m0 + (cb_only ? rest : rest >> 2);
+    Move<R> A;
+    if (code < 3)
+      load_rot<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
+    else
+      load_move21<R, C>(s.maps + 36 * c + 24, s.maps + 36 * c + 9, A);
+    if (v == 0) {
+      s.set_bbv(i, 0, c, move_apply(A, s.bbv(i, 0, c)));
+    } else if (v < 3) {
+      s.set_bbv(i, v, c, move_lin(A, s.bbv(i, v, c)));
     } else {
-      s.set_cb(i, c, apply(A, s.cb(i, c)));
+      s.set_cb(i, c, move_apply(A, s.cb(i, c)));
     }
   }
 }
@@ -725,7 +807,9 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   load_group(s, a, G, P);
   const long long t0 = a.tcount[G.chain0];
   const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
-  resync(s, a, P);
+  // decisions need Delta-E only and the exit recomputes V from scratch, so
+  // the entry and periodic resyncs rebuild the coordinates alone
+  rebuild(s, a, P);
   long long since = 0;
   const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
   unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
@@ -751,9 +835,9 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     const long long t = t0 + j;
     const int k = (int)(t % n);
     // periodic rebuild, and one at each new sweep inside a call (commits of
-    // upstream moves leave backbone atoms behind, see commit_moves)
+    // upstream moves leave torsion axes behind, see commit_moves)
     if (since >= a.resync_every || (k == 0 && j > 0)) {
-      resync(s, a, P);
+      rebuild(s, a, P);
       since = 0;
     }
     const bool fused = (k & 1) && (k + 1 < n) && (j + 1 < steps);
@@ -767,44 +851,78 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       if (a.far_skip && !dead && threadIdx.x >= 32)
         far_spheres<C>(s, f0, f1, 32, (int)blockDim.x - 32);
     }
-    if (threadIdx.x < C) {
-      const int c = threadIdx.x;
-      const int chain = G.chain0 + c;
-      const R z = s.draws[2 * ((j - d0) * C + c)], lnu = s.draws[2 * ((j - d0) * C + c) + 1];
-      const R th = s.theta[k * C + c];
-      const R thn = propose(th, z, a.sigma, a.lattice_K);
-      s.thn[c] = thn;
-      s.lnu[c] = lnu;
-      if (!dead) {
-        const R d1 = wrap_angle(thn - th);
-        V3<R> P1, Q1;
-        if (k & 1) {  // psi_i about CA_i -> C_i
-          const int i = k >> 1;
-          P1 = s.atom(i, 1, c);
-          Q1 = s.atom(i, 2, c);
-        } else {      // phi_i about N_i -> CA_i
-          const int i = k >> 1;
-          P1 = s.atom(i, 0, c);
-          Q1 = s.atom(i, 1, c);
+    if constexpr (C == 1) {
+      // one chain: three lanes share the serial step.  Lane 0 makes move 1's
+      // map A1, lane 1 move 2's map A2 about its own axis, lane 2 A1 again
+      // and then the map of move 2 about the axis as move 1 left it,
+      // composed after A1: the arithmetic of the one-lane form below in
+      // two thirds of its latency (with more chains per CTA the split
+      // measured slower)
+      const int q = threadIdx.x;
+      if (q == 0 || (q < 3 && fused)) {
+        const int k1 = q == 1 ? k + 1 : k;
+        const R z = s.draws[2 * (j + (k1 - k) - d0)];
+        const R lnu = s.draws[2 * (j + (k1 - k) - d0) + 1];
+        const R th = s.theta[k1];
+        const R thn = propose(th, z, a.sigma, a.lattice_K);
+        if (q < 2) {
+          s.thn[q] = thn;
+          s.lnu[q] = lnu;
         }
-        const Aff<R> A1 = rotation(P1, Q1, up ? -d1 : d1);
-        store_aff(s.maps + 36 * c, A1);
-        if (fused) {
-          const R z2 = s.draws[2 * ((j + 1 - d0) * C + c)];
-          const R lnu2 = s.draws[2 * ((j + 1 - d0) * C + c) + 1];
-          const R th2 = s.theta[(k + 1) * C + c];
-          const R thn2 = propose(th2, z2, a.sigma, a.lattice_K);
-          s.thn[C + c] = thn2;
-          s.lnu[C + c] = lnu2;
-          const R d2 = wrap_angle(thn2 - th2);
-          const V3<R> P2 = s.atom(p, 0, c), Q2 = s.atom(p, 1, c);  // phi_p: N_p -> CA_p
-          const Aff<R> A2 = rotation(P2, Q2, up ? -d2 : d2);
-          store_aff(s.maps + 36 * c + 12, A2);
-          // after move 1 the axis of move 2 has moved with the far side
-          const V3<R> P2m = up ? P2 : apply(A1, P2);
-          const V3<R> Q2m = up ? Q2 : apply(A1, Q2);
-          const Aff<R> A2m = rotation(P2m, Q2m, up ? -d2 : d2);
-          store_aff(s.maps + 36 * c + 24, compose(A2m, A1));
+        if (!dead) {
+          // k1 odd: psi_i about CA_i -> C_i; k1 even: phi_i about N_i -> CA_i
+          const int i = k1 >> 1;
+          const R d = wrap_angle(thn - th);
+          const Move<R> A =
+              move_rotation(s.bbv(i, 0, 0), s.bbv(i, (k1 & 1) ? 2 : 1, 0), up ? -d : d);
+          if (q < 2) {
+            store_move(s.maps + 12 * q, A, A.p);
+          } else {
+            const R z2 = s.draws[2 * (j + 1 - d0)];
+            const R th2 = s.theta[k + 1];
+            const R d2 = wrap_angle(propose(th2, z2, a.sigma, a.lattice_K) - th2);
+            const V3<R> P2 = s.bbv(p, 0, 0), u2 = s.bbv(p, 1, 0);  // phi_p: N_p -> CA_p
+            // after move 1 the axis of move 2 has moved with the far side
+            const V3<R> P2m = up ? P2 : move_apply(A, P2);
+            const V3<R> u2m = up ? u2 : move_lin(A, u2);
+            const Move<R> A21 = move_compose(move_rotation(P2m, u2m, up ? -d2 : d2), A);
+            store_move(s.maps + 24, A21, A21.q);
+          }
+        }
+      }
+    } else {
+      if (threadIdx.x < C) {
+        const int c = threadIdx.x;
+        const R z = s.draws[2 * ((j - d0) * C + c)], lnu = s.draws[2 * ((j - d0) * C + c) + 1];
+        const R th = s.theta[k * C + c];
+        const R thn = propose(th, z, a.sigma, a.lattice_K);
+        s.thn[c] = thn;
+        s.lnu[c] = lnu;
+        if (!dead) {
+          const R d1 = wrap_angle(thn - th);
+          // k odd: psi_i about CA_i -> C_i; k even: phi_i about N_i -> CA_i
+          const int i = k >> 1;
+          const Move<R> A1 =
+              move_rotation(s.bbv(i, 0, c), s.bbv(i, (k & 1) ? 2 : 1, c), up ? -d1 : d1);
+          store_move(s.maps + 36 * c, A1, A1.p);
+          if (fused) {
+            const R z2 = s.draws[2 * ((j + 1 - d0) * C + c)];
+            const R lnu2 = s.draws[2 * ((j + 1 - d0) * C + c) + 1];
+            const R th2 = s.theta[(k + 1) * C + c];
+            const R thn2 = propose(th2, z2, a.sigma, a.lattice_K);
+            s.thn[C + c] = thn2;
+            s.lnu[C + c] = lnu2;
+            const R d2 = wrap_angle(thn2 - th2);
+            const V3<R> P2 = s.bbv(p, 0, c), u2 = s.bbv(p, 1, c);  // phi_p: N_p -> CA_p
+            const Move<R> A2 = move_rotation(P2, u2, up ? -d2 : d2);
+            store_move(s.maps + 36 * c + 12, A2, A2.p);
+            // after move 1 the axis of move 2 has moved with the far side
+            const V3<R> P2m = up ? P2 : move_apply(A1, P2);
+            const V3<R> u2m = up ? u2 : move_lin(A1, u2);
+            const Move<R> A2m = move_rotation(P2m, u2m, up ? -d2 : d2);
+            const Move<R> A21 = move_compose(A2m, A1);
+            store_move(s.maps + 36 * c + 24, A21, A21.q);
+          }
         }
       }
     }
@@ -898,7 +1016,6 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE (no division)
       const int acc1 = (double)s.lnu[c] * Tc < -d1;
       int code = acc1;
-      double dE = acc1 ? d1 : 0.0;
       if (acc1) s.theta[k * C + c] = s.thn[c];
       put_trace(a, c < G.nchains, chain, t, k, acc1, s.thn[c], s.lnu[c], d1);
       int acc2 = 0;
@@ -907,12 +1024,10 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         acc2 = (double)s.lnu[C + c] * Tc < -e2;
         if (acc2) {
           code = acc1 ? 3 : 2;
-          dE += e2;
           s.theta[(k + 1) * C + c] = s.thn[C + c];
         }
         put_trace(a, c < G.nchains, chain, t + 1, k + 1, acc2, s.thn[C + c], s.lnu[C + c], e2);
       }
-      s.ecur[c] += dE;
       s.acc[c] += acc1 + acc2;
       s.commit[c] = code;
     }
@@ -966,7 +1081,7 @@ __global__ void __launch_bounds__(512) global_kernel(SweepArgs<R> a) {
 
 template <class R, int C>
 __global__ void __launch_bounds__(512) energy_kernel(SweepArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_group;
   const Layout<R, C> lay(a.Lmax, a.nmax, blockDim.x >> 5);
   Shm<R, C> s(smem, lay);

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2211_03193_gb300 import synth
-from test_gpu_parity import replay_and_compare
+from test_gpu_parity import gpu_advance, replay_and_compare
 
 pytestmark = pytest.mark.gpu
 DEG = math.pi / 180
@@ -83,13 +83,15 @@ def test_bench_workload_sampled_parity(amh, orc):
         th = th.reshape(chains, n)
         for c in range(3):
             tr = s.trace(c)
-            st = tors[c]
+            st = gst = tors[c]
             for q in range(w["cycle"]):
                 mode, T, sigma = sched.params(q)
                 seg = tr[q * n:(q + 1) * n]
                 d = replay_and_compare(orc, prot, st, seg, orc.LOCAL if mode == 0 else orc.GLOBAL,
-                                       w["window"], T, sigma, q * n, sched.seed, c, False)
+                                       w["window"], T, sigma, q * n, sched.seed, c, False,
+                                       gpu_s0=gst)
                 st = d["s_end"]
+                gst = gpu_advance(gst, seg)
             assert np.allclose(np.angle(np.exp(1j * (th[c] - st))), 0, atol=1e-4)
     for c in (0, 1, 255, 256, 511, 640, 1022, 1023):
         e = P.energy(th[c].astype(np.float64))
@@ -116,7 +118,8 @@ def test_uneven_proteins_one_context(amh, orc):
             d = replay_and_compare(orc, prots[0], tors[c * n0:(c + 1) * n0], tr[:n0], orc.LOCAL,
                                    8, T, sigma, 0, 9, c, False)
             replay_and_compare(orc, prots[0], d["s_end"], tr[n0:], orc.GLOBAL, 0, T, sigma, n0,
-                               9, c, False)
+                               9, c, False,
+                               gpu_s0=gpu_advance(tors[c * n0:(c + 1) * n0], tr[:n0]))
         for p in (0, 7, 21, 40, 63):
             off = s.offsets[p]
             n = prots[p].n
