@@ -814,6 +814,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
   unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
   long long d0 = 0, dend = 0;  // proposals [d0, dend) have their draws in s.draws
+  int kn = (int)(t0 % n);      // torsion index of proposal t0 + j (kept without a 64-bit modulo)
   for (long long j = 0; j < steps;) {
     if (j + 2 > dend) {
       // the Philox draws of the next kDraw proposals, by all threads (they
@@ -833,7 +834,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       __syncthreads();
     }
     const long long t = t0 + j;
-    const int k = (int)(t % n);
+    const int k = kn;
     // periodic rebuild, and one at each new sweep inside a call (commits of
     // upstream moves leave torsion axes behind, see commit_moves)
     if (since >= a.resync_every || (k == 0 && j > 0)) {
@@ -940,6 +941,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       __syncthreads();
       j += 1;
       since += 1;
+      kn = k + 1 < n ? k + 1 : 0;
       continue;
     }
     if constexpr (ST) {
@@ -1035,6 +1037,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     commit_moves(s, m0, m1, up);
     __syncthreads();
     j += fused ? 2 : 1;
+    kn = k + (fused ? 2 : 1);
+    if (kn >= n) kn -= n;
     since += fused ? 2 : 1;
   }
   // exit: the energy from scratch (FP64 sum); the FP32 form takes the
