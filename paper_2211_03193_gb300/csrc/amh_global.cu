@@ -487,8 +487,14 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   const Pt4<float>* __restrict__ fsph = s.fsph;
   ChunkBits* __restrict__ bits = s.bits;
   // (2) one thread per (moving atom, chain): the images' sphere and the
-  // chunks within reach, as bits
-  for (int t = threadIdx.x; t < nM * C; t += blockDim.x) {
+  // chunks within reach, as bits.  With one chain each thread takes the
+  // contiguous range of moving atoms that it lists in (3), so it reads
+  // back only its own bits and no barrier is needed between the two.
+  const int per = (nM + blockDim.x - 1) / blockDim.x;
+  const int b0 = min(nM, (int)threadIdx.x * per), b1 = min(nM, b0 + per);
+  const int t_beg = C == 1 ? b0 : (int)threadIdx.x, t_end = C == 1 ? b1 : nM * C;
+  const int t_step = C == 1 ? 1 : (int)blockDim.x;
+  for (int t = t_beg; t < t_end; t += t_step) {
     const int mi = t / C, c = t - mi * C;
     ChunkBits b = 0;
     if ((real >> c) & 1u) {
@@ -518,7 +524,7 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
     }
     bits[c * nMs + mi] = b;
   }
-  __syncthreads();
+  if constexpr (C > 1) __syncthreads();
   // (3) the items kept for any chain, in item order (a block-wide scan of
   // their counts per moving atom)
   auto kept = [&](int mi) {
@@ -527,8 +533,6 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
     for (int c = 0; c < C; ++c) w |= bits[c * nMs + mi];
     return w;
   };
-  const int per = (nM + blockDim.x - 1) / blockDim.x;
-  const int b0 = min(nM, (int)threadIdx.x * per), b1 = min(nM, b0 + per);
   int mine = 0;
   for (int mi = b0; mi < b1; ++mi) mine += __popcll(kept(mi));
   int incl = mine;
@@ -710,17 +714,19 @@ __device__ void commit_moves(Shm<R, C>& s, int m0, int m1, bool cb_only) {
   // axes (a new sweep starts from a rebuild), so only the C-betas move
   const int per = cb_only ? 1 : 4;
   const int total = (m1 - m0) * per * C;
+  // the block size is a multiple of C: a thread's items all belong to
+  // chain slot threadIdx.x % C, so it loads that slot's move once
+  const int c = threadIdx.x % C;
+  const int code = s.commit[c];
+  if (!code) return;
+  Move<R> A;
+  if (code < 3)
+    load_rot<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
+  else
+    load_move21<R, C>(s.maps + 36 * c + 24, s.maps + 36 * c + 9, A);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int c = idx % C;
-    const int code = s.commit[c];
-    if (!code) continue;
     const int rest = idx / C;
     const int v = cb_only ? 3 : rest & 3, i = m0 + (cb_only ? rest : rest >> 2);
-    Move<R> A;
-    if (code < 3)
-      load_rot<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
-    else
-      load_move21<R, C>(s.maps + 36 * c + 24, s.maps + 36 * c + 9, A);
     if (v == 0) {
       s.set_bbv(i, 0, c, move_apply(A, s.bbv(i, 0, c)));
     } else if (v < 3) {
