@@ -268,8 +268,16 @@ def test_far_field_skip_equals_dense(amh, orc, C, wide):
                          resync_every=30 if wide else 60,
                          trace_chains=chains, trace_capacity=steps) as s:
             s.sweep(1, 0, T, sigma, steps, seed)
-            runs.append(([s.trace(c) for c in range(chains)], s.state()[1]))
-    (tf, Ef), (td, Ed) = runs
+            th_end, E_end = s.state()[:2]
+            runs.append(([s.trace(c) for c in range(chains)], E_end, th_end.reshape(chains, -1)))
+    (tf, Ef, thf), (td, Ed, thd) = runs
+    # the energy a call ends with (with skipping: flat chunks added from the
+    # protein's flat sums) against the oracle's V of the final torsions
+    P = orc.Problem(L, prot.p, prot.edges)
+    for c in range(chains):
+        for E_end, th_end in ((Ef, thf), (Ed, thd)):
+            e = P.energy(f64(th_end[c]))
+            assert abs(E_end[c] - e) <= 1e-5 * abs(e), c
     k = tf[0]["k"]
     p = (k + 1) // 2
     npairs = p * (L - p)
