@@ -184,19 +184,24 @@ amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, dou
 /*
  * amh_get_state -- copy out the chains' state; any pointer may be NULL.
  *   torsions_out, best_torsions  [sum chains * 2 L] float32 (host or device)
- *   E_out      energy after the last global sweep / energy call [chains]
+ *   E_out      V as of the last global sweep or amh_energy call [chains];
+ *              after amh_set_state / amh_noisy_restart (with no global
+ *              sweep since) V of the current state, computed by this call
  *   best_E     lowest energy seen at a global-sweep end [chains]
  */
 amh_status amh_get_state(amh_ctx* ctx, float* torsions_out, double* E_out, double* best_E,
                          float* best_torsions);
 
 /* amh_set_state -- replace every chain's torsions (host or device, float32,
- * layout as in amh_init) and recompute V.  Counters and best are kept.     */
+ * layout as in amh_init; a host buffer may be reused when the call returns).
+ * V is recomputed when next read (amh_get_state, amh_exchange), unless a
+ * global sweep, which ends with V from scratch, comes first.  Counters and
+ * best are kept.                                                            */
 amh_status amh_set_state(amh_ctx* ctx, const float* torsions);
 
 /* amh_noisy_restart -- s_k += sd_rad * z for every torsion of every chain,
  * z from Philox counter (chain, k, 0, 1) under key `seed`, then wrap; V is
- * recomputed (the noisy-restart baseline of Sec. 3).                       */
+ * recomputed as after amh_set_state (the noisy-restart baseline of Sec. 3). */
 amh_status amh_noisy_restart(amh_ctx* ctx, double sd_rad, unsigned long long seed);
 
 /*
@@ -217,7 +222,8 @@ amh_status amh_set_ladder(amh_ctx* ctx, int K, const double* ladder);
  * ladder[j] (the Metropolis rule for exchanging two replicas), u from
  * Philox4x32-10 at counter (chain of slot j, round low, round high, 3)
  * where round counts this context's exchange calls.  Uses the stored
- * energies: call it after a global sweep or amh_energy.  swapped_out: NULL
+ * energies (recomputed first if the state was replaced since the last global
+ * sweep or amh_energy): call it after a global sweep.  swapped_out: NULL
  * or [total chains] long long (host or device), 1 at the lower slot of each
  * swapped pair.
  */

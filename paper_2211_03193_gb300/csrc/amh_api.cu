@@ -59,6 +59,9 @@ struct amh_ctx {
   size_t smem_optin = 0;
   std::string msg;
   bool broken = false;
+  // E_cur is owed a recomputation: the state was replaced (amh_set_state,
+  // amh_noisy_restart) and no global sweep or energy call has run since
+  bool energy_stale = false;
 };
 
 namespace {
@@ -768,11 +771,21 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   return AMH_OK;
 }
 
+// Recompute E_cur if the state was replaced since it was last computed.
+static amh_status fresh_energy(amh_ctx* ctx) {
+  if (!ctx->energy_stale) return AMH_OK;
+  amh_status st = ctx->precision == 64 ? run_energy<double>(ctx) : run_energy<float>(ctx);
+  if (st) return st;
+  ctx->energy_stale = false;
+  return AMH_OK;
+}
+
 amh_status amh_energy(amh_ctx* ctx, double* E_out) {
   amh_status st = check_ctx(ctx);
   if (st) return st;
   st = ctx->precision == 64 ? run_energy<double>(ctx) : run_energy<float>(ctx);
   if (st) return st;
+  ctx->energy_stale = false;
   if (E_out) {
     CK(ctx, cudaMemcpyAsync(E_out, ctx->E_cur, sizeof(double) * ctx->total_chains,
                             cudaMemcpyDefault, ctx->stream));
@@ -803,6 +816,7 @@ static amh_status sweep_common(amh_ctx* ctx, int mode, int window, double T, dou
              ? sweep_impl<double>(ctx, mode, window, T, sigma, steps, are_sweeps, seed)
              : sweep_impl<float>(ctx, mode, window, T, sigma, steps, are_sweeps, seed);
     if (st) return st;
+    if (mode == AMH_GLOBAL) ctx->energy_stale = false;  // every chain ends with V from scratch
   } else {
     CK(ctx, cudaMemsetAsync(ctx->acc, 0, sizeof(long long) * ctx->total_chains, ctx->stream));
   }
@@ -875,6 +889,8 @@ amh_status amh_get_state(amh_ctx* ctx, float* torsions_out, double* E_out, doubl
   st = out_tors(ctx->best_theta, best_torsions);
   if (st) return st;
   if (E_out) {
+    st = fresh_energy(ctx);
+    if (st) return st;
     CK(ctx, cudaMemcpyAsync(E_out, ctx->E_cur, sizeof(double) * ctx->total_chains,
                             cudaMemcpyDefault, ctx->stream));
     if (!is_device_ptr(E_out)) host = true;
@@ -893,16 +909,16 @@ amh_status amh_set_state(amh_ctx* ctx, const float* torsions) {
   if (st) return st;
   if (!torsions) return set_err(ctx, AMH_EINVAL, "torsions is NULL");
   const long long nt = ctx->tors_total;
-  CK(ctx, cudaMemcpyAsync(ctx->f32buf, torsions, sizeof(float) * nt, cudaMemcpyDefault,
-                          ctx->stream));
   if (ctx->precision == 64) {
+    CK(ctx, cudaMemcpyAsync(ctx->f32buf, torsions, sizeof(float) * nt, cudaMemcpyDefault,
+                            ctx->stream));
     CK(ctx, launch_convert_in<double>(ctx->f32buf, (double*)ctx->theta, nt, ctx->stream));
-    st = run_energy<double>(ctx);
   } else {
-    CK(ctx, launch_convert_in<float>(ctx->f32buf, (float*)ctx->theta, nt, ctx->stream));
-    st = run_energy<float>(ctx);
+    // the FP32 form holds the torsions as given: one copy, no conversion
+    CK(ctx, cudaMemcpyAsync(ctx->theta, torsions, sizeof(float) * nt, cudaMemcpyDefault,
+                            ctx->stream));
   }
-  if (st) return st;
+  ctx->energy_stale = true;  // V is recomputed when next read, unless a global sweep does it
   if (!is_device_ptr(torsions)) CK(ctx, cudaStreamSynchronize(ctx->stream));
   return AMH_OK;
 }
@@ -911,14 +927,14 @@ amh_status amh_noisy_restart(amh_ctx* ctx, double sd_rad, unsigned long long see
   amh_status st = check_ctx(ctx);
   if (st) return st;
   if (!std::isfinite(sd_rad) || sd_rad < 0) return set_err(ctx, AMH_EINVAL, "bad sd");
-  if (ctx->precision == 64) {
+  if (ctx->precision == 64)
     CK(ctx, launch_noisy<double>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains, ctx->nmax,
                                  (double*)ctx->theta, sd_rad, seed, ctx->stream));
-    return run_energy<double>(ctx);
-  }
-  CK(ctx, launch_noisy<float>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains, ctx->nmax,
-                              (float*)ctx->theta, (float)sd_rad, seed, ctx->stream));
-  return run_energy<float>(ctx);
+  else
+    CK(ctx, launch_noisy<float>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains, ctx->nmax,
+                                (float*)ctx->theta, (float)sd_rad, seed, ctx->stream));
+  ctx->energy_stale = true;  // V is recomputed when next read, unless a global sweep does it
+  return AMH_OK;
 }
 
 amh_status amh_get_trace(amh_ctx* ctx, int chain, amh_trace_rec* out, long long* count) {
@@ -972,6 +988,8 @@ amh_status amh_exchange(amh_ctx* ctx, double T, int parity, unsigned long long s
   if (!ctx->ladder_K) return set_err(ctx, AMH_EINVAL, "no temperature ladder set");
   if (!(T > 0) || !std::isfinite(T) || (parity != 0 && parity != 1))
     return set_err(ctx, AMH_EINVAL, "T must be positive and parity 0 or 1");
+  st = fresh_energy(ctx);
+  if (st) return st;
   if (ctx->precision == 64) {
     CK(ctx, launch_exchange<double>(ctx->prot_d, ctx->chain_prot_d, ctx->total_chains,
                                     ctx->ladder_K, ctx->ladder, T, parity, seed, ctx->xround,

@@ -416,6 +416,38 @@ def test_grad_matches_oracle(amh, orc, precision):
 
 
 # ---------------------------------------------------------------- noisy restart
+def test_state_change_energy_on_read(amh, orc):
+    """After amh_set_state or a noisy restart, V is computed when next read
+    (or by a global sweep): the energies read back are always the oracle's
+    V of the torsions read back, with or without sweeps in between."""
+    L, chains = 40, 4
+    prot = synth.make_protein(L, seed=520)
+    tors = synth.random_torsions(chains, L, seed=521)
+    new = synth.random_torsions(chains, L, seed=522)
+    P = orc.Problem(L, prot.p, prot.edges)
+
+    def check(s):
+        th, E = s.state()[:2]
+        th = th.reshape(chains, -1)
+        for c in range(chains):
+            e = P.energy(f64(th[c]))
+            assert abs(E[c] - e) <= 1e-5 * abs(e), c
+        return th
+
+    with amh.Sampler(prot, chains, tors) as s:
+        s.set_state(np.asarray(new, dtype=np.float32).ravel())
+        th = check(s)
+        assert np.array_equal(th, np.asarray(new, dtype=np.float32))
+        s.set_state(np.asarray(tors, dtype=np.float32).ravel())
+        s.sweeps(0, 8, 1.0, 10 * DEG, 1, 3)   # a local sweep leaves V to the read
+        check(s)
+        s.noisy_restart(0.2, 5)
+        s.sweeps(1, 0, 1.0, 10 * DEG, 1, 3)   # a global sweep ends with V
+        check(s)
+        s.noisy_restart(0.2, 6)
+        check(s)
+
+
 def test_noisy_restart_matches_oracle(amh, orc):
     L, chains = 12, 5
     prot = synth.make_protein(L, seed=600)
