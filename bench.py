@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--threads", type=int, default=0, help="global-sweep threads per CTA")
     ap.add_argument("--texture", type=int, default=0,
                     help="table entries: 0 default (texture when it fits), 1 texture, 2 loads")
+    ap.add_argument("--local-chains-per-cta", type=int, default=0,
+                    help="local-sweep chains per CTA (0 = chosen from the window)")
+    ap.add_argument("--local-threads", type=int, default=0, help="local-sweep threads per CTA")
     ap.add_argument("--stage", type=int, default=0,
                     help="table rows: 0 tuned, 1 staged in shared memory, 2 through L1")
     return ap.parse_args()
@@ -566,7 +569,8 @@ def run_ours(args):
     aux = torch.cuda.Stream(priority=0)
     samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
-                   stage_table=args.stage, table_texture=args.texture, far_pairs=args.far_pairs)
+                   stage_table=args.stage, table_texture=args.texture, far_pairs=args.far_pairs,
+                   local_chains_per_cta=args.local_chains_per_cta, local_threads=args.local_threads)
     # a context for the gradient pass only (fixed launch shape: no autotuning)
     gsamp = Sampler(prot, 1, tors[:1], precision=w["precision"], stream=aux, chains_per_cta=1,
                     threads_per_cta=128)

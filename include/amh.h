@@ -86,6 +86,13 @@ typedef struct {
                               so Delta V is unchanged; found per 12-atom chunk
                               of the fixed side by bounding spheres) (default);
                               1 = evaluate every straddle pair. */
+  int local_chains_per_cta; /* local sweeps: chains per CTA, 0 (chosen from the
+                              window: as many as keep one colour's windows
+                              within 256 threads) or 1, 2, 4, 8, 16, 32 */
+  int local_threads;       /* local sweeps: threads per CTA, 0 (256, fewer if
+                              shared memory is short) or a multiple of 32 up
+                              to 256; AMH_EINVAL at the sweep if the shape
+                              does not fit in shared memory */
   void* stream;            /* cudaStream_t; NULL = the legacy default stream */
 } amh_options;
 

@@ -33,7 +33,8 @@ class amh_options(ctypes.Structure):
                 ("trace_chains", ctypes.c_int), ("trace_capacity", ctypes.c_longlong),
                 ("lattice_K", ctypes.c_int), ("table_is_neglog", ctypes.c_int),
                 ("stage_table", ctypes.c_int), ("table_texture", ctypes.c_int),
-                ("far_pairs", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("far_pairs", ctypes.c_int), ("local_chains_per_cta", ctypes.c_int),
+                ("local_threads", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class amh_trace_rec(ctypes.Structure):

@@ -547,7 +547,16 @@ amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma
     const size_t room = ctx->smem_optin - kStaticSmemMargin;
     int threads = 256;
     size_t sm = 0;
-    for (; q >= 0; --q) {
+    if (ctx->opt.local_chains_per_cta || ctx->opt.local_threads) {
+      // a given shape
+      q = 0;
+      if (ctx->opt.local_chains_per_cta)
+        while ((1 << q) < ctx->opt.local_chains_per_cta) ++q;
+      threads = ctx->opt.local_threads ? ctx->opt.local_threads : 256;
+      sm = local_smem_bytes<R>(ctx->nmax, 1 << q, threads, window);
+      if (sm > room) return set_err(ctx, AMH_EINVAL, "local launch shape does not fit shared memory");
+    }
+    for (; q >= 0 && !ctx->opt.local_chains_per_cta && !ctx->opt.local_threads; --q) {
       threads = 256;
       for (;;) {
         sm = local_smem_bytes<R>(ctx->nmax, 1 << q, threads, window);
@@ -614,6 +623,8 @@ void amh_options_default(amh_options* opt) {
   opt->stage_table = 0;
   opt->table_texture = 0;
   opt->far_pairs = 0;
+  opt->local_chains_per_cta = 0;
+  opt->local_threads = 0;
   opt->stream = nullptr;
 }
 
@@ -647,6 +658,11 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
     return set_err(nullptr, AMH_EINVAL, "stage_table must be 0, 1 or 2");
   if (o.far_pairs < 0 || o.far_pairs > 1)
     return set_err(nullptr, AMH_EINVAL, "far_pairs must be 0 or 1");
+  if (o.local_chains_per_cta < 0 || o.local_chains_per_cta > kLocalMaxChains ||
+      (o.local_chains_per_cta & (o.local_chains_per_cta - 1)))
+    return set_err(nullptr, AMH_EINVAL, "local_chains_per_cta must be 0, 1, 2, 4, 8, 16 or 32");
+  if (o.local_threads < 0 || o.local_threads > 256 || o.local_threads % 32)
+    return set_err(nullptr, AMH_EINVAL, "local_threads must be 0 or a multiple of 32 up to 256");
   if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)
     return set_err(nullptr, AMH_EINVAL, "negative option");
   // bins: evenly spaced centres

@@ -25,7 +25,8 @@ class Sampler:
     def __init__(self, proteins, chains, torsions, precision: int = 32, resync_every: int = 1000,
                  chains_per_cta: int = 0, threads_per_cta: int = 0, trace_chains: int = 0,
                  trace_capacity: int = 0, lattice_K: int = 0, stage_table: int = 0,
-                 table_texture: int = 0, far_pairs: int = 0, stream=None):
+                 table_texture: int = 0, far_pairs: int = 0, local_chains_per_cta: int = 0,
+                 local_threads: int = 0, stream=None):
         if not isinstance(proteins, (list, tuple)):
             proteins = [proteins]
         chains = list(np.atleast_1d(chains).astype(int))
@@ -55,7 +56,9 @@ class Sampler:
                                        threads_per_cta=threads_per_cta, trace_chains=trace_chains,
                                        trace_capacity=trace_capacity, lattice_K=lattice_K,
                                        stage_table=stage_table, table_texture=table_texture,
-                                       far_pairs=far_pairs, stream=stream)
+                                       far_pairs=far_pairs,
+                                       local_chains_per_cta=local_chains_per_cta,
+                                       local_threads=local_threads, stream=stream)
         self.ctx = _amh.amh_init(np.array(self.L), np.array(chains), torsions, table, edges, opt)
         self.precision = precision
 

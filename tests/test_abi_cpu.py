@@ -68,6 +68,10 @@ def _init(lib, **over):
     dict(opt=dict(chains_per_cta=3)),
     dict(opt=dict(threads_per_cta=96)),
     dict(opt=dict(far_pairs=2)),
+    dict(opt=dict(local_chains_per_cta=3)),
+    dict(opt=dict(local_chains_per_cta=64)),
+    dict(opt=dict(local_threads=48)),
+    dict(opt=dict(local_threads=512)),
     dict(opt=dict(table_texture=3)),
     dict(opt=dict(stage_table=-1)),
 ])
@@ -90,6 +94,7 @@ def test_options_default_far_field_skip_on():
     from paper_2211_03193_gb300 import _amh
     o = _amh.amh_options_default()
     assert o.far_pairs == 0 and o.table_texture == 0 and o.threads_per_cta == 0
+    assert o.local_chains_per_cta == 0 and o.local_threads == 0
 
 
 def test_peaks_library_exports_its_symbol():
