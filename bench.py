@@ -674,11 +674,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for _ in range(args.steps):
-                _amh.amh_set_state(samp.ctx, h_in)
+            # two pinned buffers in turn: a step's result is the next step's input
+            bufs = (h_in, h_out)
+            for i in range(args.steps):
+                _amh.amh_set_state(samp.ctx, bufs[i % 2])
                 cycle()
-                _amh.amh_get_state(samp.ctx, h_out, h_E, h_bE, None)
-                h_in.copy_(h_out)
+                _amh.amh_get_state(samp.ctx, bufs[(i + 1) % 2], h_E, h_bE, None)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         e2e = {"value": props_step * args.steps * world / dt, "unit": "proposals/s",
