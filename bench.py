@@ -123,7 +123,7 @@ def pair_evals_per_cycle(w):
     """Pair-term evaluations one chain performs in one cycle."""
     L, n, h = w["L"], w["n"], w["window"] // 2
     glob = 2 * (L ** 3 - L) // 3          # old + new of every straddle pair
-    resync = 2 * (L * (L - 1) // 2)       # entry and exit resync
+    resync = L * (L - 1) // 2             # the exit energy (the entry rebuild forms coordinates only)
     loc = 0
     for k in range(n):
         c, p = k // 2, (k + 1) // 2
@@ -705,9 +705,9 @@ def run_ours(args):
     g_ms = float(np.mean(glob_ms)) if glob_ms else float("nan")
     # terms per global launch: the straddle blocks' (all of them with
     # --far-pairs 1, else those not skipped as flat; counted by the library)
-    # plus the entry and exit resyncs' full energies
+    # plus the full energy each call ends with
     dense = 2 * (L ** 3 - L) // 3 * chains
-    resync_terms = 2 * (L * (L - 1) // 2) * chains
+    resync_terms = (L * (L - 1) // 2) * chains
     evals_glob_launch = int(terms_glob) + resync_terms
     achieved = evals_glob_launch * FLOP_PER_EVAL / (g_ms / 1000.0) / 1e12
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
