@@ -53,9 +53,11 @@ typedef enum {
 
 typedef struct {
   int precision;           /* 32 (default): FP32 coordinates and pair terms,
-                              FP64 running energy; 64: FP64 throughout. */
-  int resync_every;        /* global sweeps rebuild G(s) and recompute V in
-                              FP64 every this many proposals (default 1000). */
+                              energies summed in FP64; 64: FP64 throughout. */
+  int resync_every;        /* global sweeps rebuild G(s) in FP64 from the
+                              torsions every this many proposals (default
+                              1000), at entry and at each new sweep; V is
+                              recomputed from scratch when a call ends. */
   int chains_per_cta;      /* chains that share one CTA in global sweeps:
                               0 = autotuned at first use, else 1, 2, 4 or 8. */
   int threads_per_cta;     /* global sweeps: 0 = autotuned with chains_per_cta
@@ -160,7 +162,9 @@ amh_status amh_energy(amh_ctx* ctx, double* E_out);
  *                    and are evaluated concurrently.
  *   accepted_out     NULL, or [total chains] long long (host or device):
  *                    accepted proposals of this call per chain.
- * Global sweeps end with an FP64 resync and update each chain's best state.
+ * Global sweeps end with V recomputed from scratch (FP32 terms of the current
+ * coordinates, FP64 sum; FP64 form: G(s) rebuilt first) and update each
+ * chain's best state.
  * Split calls equal one long call (the counter continues).
  */
 amh_status amh_sweep(amh_ctx* ctx, int mode, int window, double T, double sigma_rad,
