@@ -20,6 +20,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -90,6 +91,9 @@ def parse():
     ap.add_argument("--local-threads", type=int, default=0, help="local-sweep threads per CTA")
     ap.add_argument("--stage", type=int, default=0,
                     help="table rows: 0 tuned, 1 staged in shared memory, 2 through L1")
+    ap.add_argument("--clocks-csv", default="",
+                    help="keep the nvidia-smi clock samples of the timed region in this file "
+                         "(default: a temporary file, removed after it is summarised)")
     return ap.parse_args()
 
 
@@ -144,14 +148,20 @@ def peaks():
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.keep = bool(path)
+        if path:
+            self.path = path
+        else:
+            fd, self.path = tempfile.mkstemp(prefix="amh_clocks_", suffix=".csv")
+            os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
@@ -178,6 +188,12 @@ class Clocks:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
         except Exception:
             return None
+        finally:
+            if not self.keep:
+                try:
+                    os.unlink(self.path)
+                except OSError:
+                    pass
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -638,7 +654,7 @@ def run_ours(args):
     step_ms = []
     glob_ev = []
     terms0 = samp.pair_terms()  # straddle-pair terms evaluated so far (synchronises)
-    with Clocks(local) as clk:
+    with Clocks(local, args.clocks_csv or None) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(float(len(step_ms)))  # evict L2 between timed steps

@@ -285,10 +285,14 @@ void amh_destroy(amh_ctx* ctx);
  * amh_grad_noalloc -- amh_grad without a context and without allocating.
  * (The paper has no counterpart: this is a deployment variant.)
  *
- * For callers that must not call cudaMalloc: code that runs while a CUDA
- * graph is being captured (allocation is not a capturable operation), hosts
- * whose device memory belongs to a pool or caching allocator they do not
- * control, and services with a fixed device-memory budget.  amh_grad reads a
+ * For callers that must not call cudaMalloc: hosts whose device memory
+ * belongs to a pool or caching allocator they do not control (a framework
+ * that reserves the GPU's memory up front leaves nothing for a second
+ * allocator, and allocating beside it fragments its pool), services that
+ * run under a fixed device-memory budget decided at start-up (an allocation
+ * later can fail in the middle of a run), and latency-bound loops that
+ * cannot afford the device-wide synchronisation cudaMalloc and cudaFree may
+ * imply.  amh_grad reads a
  * distogram table that amh_init prepared in device memory the library
  * allocated; here the table is prepared on every call into one static
  * device array of AMH_NOALLOC_MAX_ENTRIES (value, slope) entries of 8 bytes

@@ -10,8 +10,10 @@
 // e(x), e(A1 x), e(A2 x) and e(A21 x) per pair give Delta-E of move 1 and
 // of move 2 after either outcome of move 1, exactly as in sequential
 // order.  The moving side of a proposal is the smaller one (energy is
-// invariant under rigid motion).  The running energy is kept in FP64 and
-// rebuilt from G(s) every resync_every proposals and at the end of a call.
+// invariant under rigid motion).  No running energy is kept (a decision
+// needs Delta-E only): the coordinates are rebuilt from the torsions in FP64
+// at entry, every resync_every proposals and at each new sweep, and V is
+// recomputed from scratch (FP64 sum) when the call ends.
 #include "amh_internal.h"
 
 namespace amh {

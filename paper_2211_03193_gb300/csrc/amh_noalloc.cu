@@ -97,21 +97,30 @@ extern "C" amh_status amh_grad_noalloc(int L, int B, const double* table, int ta
     scratch = g_table_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
+  size_t optin = 0;
   {
     static bool smem_set[kMaxDevices] = {false};
+    static size_t smem_optin[kMaxDevices] = {0};
     std::lock_guard<std::mutex> lk(g_mu);
     if (!smem_set[dev]) {
       cudaDeviceProp prop;
       e = cudaGetDeviceProperties(&prop, dev);
       if (e == cudaSuccess) e = grad_set_smem<float>(prop.sharedMemPerBlockOptin);
       if (e != cudaSuccess) return fail(AMH_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+      smem_optin[dev] = prop.sharedMemPerBlockOptin;
       smem_set[dev] = true;
     }
+    optin = smem_optin[dev];
   }
+  // the gradient kernel keeps one chain's coordinates in shared memory: the
+  // same limit amh_grad applies (1 KB left for its static shared memory)
+  if (grad_smem_bytes(sizeof(float), L) + 1024 > optin)
+    return fail(AMH_EINVAL, "L = " + std::to_string(L) + " is too long for the gradient "
+                                "kernel's shared memory");
   e = launch_prep_table<float>(table, rows, B, Bp, table_is_neglog, (float*)scratch, st);
   if (e != cudaSuccess) return fail(AMH_ECUDA, std::string("table kernel: ") + cudaGetErrorString(e));
 
-  Tab<float> tb;
+  Tab<float> tb{};  // tex = 0: the gradient kernel reads entries by plain loads
   tb.E = scratch;
   tb.inv_w = (float)(1.0 / w);
   tb.off = (float)(-cen[0] / w);

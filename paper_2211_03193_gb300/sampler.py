@@ -158,9 +158,9 @@ class Schedule:
     sigma_s linear from sigma0 to sigma1 (degrees) over the S sweeps; both
     constant within a sweep.  n_local = 0 gives plain MH; noisy_every > 0
     adds a Gaussian kick of noisy_sd_deg to every torsion every that many
-    sweeps (MH with noisy restarts).  windows (optional) cascades several
-    localization radii (Sec. 2.2: "one can cascade multiple localization
-    ranges"): local sweep j of a cycle uses windows[j % len(windows)]."""
+    sweeps (MH with noisy restarts).  windows (optional) cycles through
+    several localization radii in turn (the cascaded radii of Sec. 2.2):
+    local sweep j of a cycle uses windows[j % len(windows)]."""
     total_sweeps: int
     n_local: int = 10
     n_global: int = 1

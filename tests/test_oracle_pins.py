@@ -4,6 +4,8 @@ Each test checks the oracle against something other than itself: closed
 forms, invariants, brute force on tiny inputs, an independently written
 dihedral formula, or exact enumeration.  None needs a GPU.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -309,6 +311,19 @@ def test_teacher_forcing_follows_given_decisions(orc):
 
 
 # ---------------------------------------------------------------- RNG
+def test_philox_known_answers(orc):
+    """The oracle's Philox4x32-10 reproduces the generator's published
+    known-answer vectors (tests/golden/philox4x32_10_kat.txt): a wrong
+    multiplier, Weyl constant, round count or word order fails every row."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        got = orc.philox(v[0:4], v[4:6])
+        assert [int(x) for x in got] == v[6:10], (r, ["%08x" % x for x in got])
+
+
 def test_philox_words_are_uniform_and_decorrelated(orc):
     words = np.array([orc.philox((c, 7, 0, 0), (123, 456)) for c in range(20000)])
     bytes_ = words.view(np.uint8).ravel()

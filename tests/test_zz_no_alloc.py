@@ -1,8 +1,10 @@
 """amh_grad_noalloc: the gradient entry point for callers that cannot
-allocate device memory (for example code running while a CUDA graph is
-captured, or hosts whose device memory belongs to an allocator they do not
-control).  Its output must match amh_grad's, call after call, although the
-prepared table now lives in one static device array that every call shares.
+allocate device memory (hosts whose device memory belongs to a pool or
+caching allocator they do not control, services with a fixed device-memory
+budget).  It runs the same table preparation and gradient kernels as
+amh_grad, so its output must equal amh_grad's bit for bit, call after call,
+although the prepared table now lives in one static device array that every
+call shares.
 
 Collected last on purpose: if it fails, a run that stops at the first
 failure has already run every other test.
@@ -45,10 +47,9 @@ def test_noalloc_matches_amh_grad_on_two_calls_in_a_row(mods):
         g = torch.empty_like(theta)
         amh.amh_grad_noalloc(L, prot.B, table, 0, prot.edges, theta, batch, E, g)
         torch.cuda.synchronize()
-        # the tolerance the FP32 gradient tests use against the FP64 oracle
-        assert torch.all((E - E_ref).abs() <= 1e-5 * E_ref.abs())
-        for b in range(batch):
-            assert torch.linalg.norm(g[b] - g_ref[b]) <= 1e-3 * torch.linalg.norm(g_ref[b])
+        # the same kernels on the same prepared entries: identical results
+        assert torch.equal(E, E_ref)
+        assert torch.equal(g, g_ref)
 
 
 def test_noalloc_repeated_calls_are_stable_and_neglog_input(mods):
@@ -66,8 +67,21 @@ def test_noalloc_repeated_calls_are_stable_and_neglog_input(mods):
         amh.amh_grad_noalloc(L, prot.B, tab, flag, prot.edges, theta, batch, E, g)
         torch.cuda.synchronize()
         outs.append((E, g))
-        assert torch.all((E - E_ref).abs() <= 1e-5 * E_ref.abs())
-        assert torch.linalg.norm(g - g_ref) <= 1e-3 * torch.linalg.norm(g_ref)
+        if flag == 0:
+            assert torch.equal(E, E_ref) and torch.equal(g, g_ref)
+        else:
+            # -ln p given directly: the entries differ from the p path only
+            # by the rounding of the log, so the results agree to FP32 level
+            assert torch.all((E - E_ref).abs() <= 1e-6 * E_ref.abs())
+            assert torch.linalg.norm(g - g_ref) <= 1e-5 * torch.linalg.norm(g_ref)
+    # further calls allocate nothing: the device's free memory stays put
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        amh.amh_grad_noalloc(L, prot.B, table, 0, prot.edges, theta, batch, outs[0][0],
+                             outs[0][1])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(outs[0][0], E_ref) and torch.equal(outs[0][1], g_ref)
 
 
 def test_noalloc_rejects_tables_beyond_the_static_array(mods):
