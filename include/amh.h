@@ -24,8 +24,9 @@
  *  - All work is issued on the context's stream (amh_options.stream).
  *    Calls whose output is host memory synchronise that stream; calls
  *    whose outputs are device memory (or NULL) return without waiting.
- *  - A CUDA error makes the context sticky-broken: that call returns
- *    AMH_ECUDA and every later call AMH_ESTATE until amh_destroy.
+ *  - A CUDA error or a bounded device wait that gave up makes the context
+ *    sticky-broken: that call returns AMH_ECUDA (or AMH_ETIMEOUT) and every
+ *    later call AMH_ESTATE until amh_destroy.
  *  - A context is used from one host thread at a time.
  */
 #ifndef AMH_H
@@ -96,6 +97,17 @@ typedef struct {
                               to 256; AMH_EINVAL at the sweep if the shape
                               does not fit in shared memory */
   void* stream;            /* cudaStream_t; NULL = the legacy default stream */
+  int keep_coords;         /* 1: keep every chain's C-beta coordinates for
+                              amh_get_coords (one buffer of 3 L values per
+                              chain, written by global sweeps and energy
+                              computations); 0 (default): not kept */
+  int wait_test;           /* test hook of the bounded waits (0 = off, the
+                              default).  N > 0: every CTA of a staged global
+                              sweep first waits on its staging ring's first
+                              slot before issuing any copy, giving up after N
+                              tries.  Nothing can arrive there, so the wait
+                              gives up with no copy in flight and the call
+                              fails with AMH_ETIMEOUT. */
 } amh_options;
 
 /* One proposal record (traced chains only), 32 bytes. */
@@ -269,6 +281,37 @@ amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated);
 amh_status amh_philox(unsigned long long seed, unsigned chain, unsigned long long t0,
                       unsigned stream, long long count, unsigned* words_out, float* z_out,
                       float* u_out);
+
+/*
+ * amh_get_coords -- the C-beta coordinates x = G(s) the context holds
+ * (Sec. 2.1: x = G(s) defines the coordinates of all C-beta atoms), for
+ * checking the builder and the moves against an independent G(s).  Needs
+ * keep_coords = 1 at amh_init, else AMH_EINVAL.
+ *   cb_out  host, double [sum over chains of L_p][3], chain by chain.
+ * The coordinates are those of the last global sweep or energy computation
+ * (the ones its V was summed from), widened from the context's precision:
+ * after a global sweep, the coordinates the sweep ended with (rebuilt at
+ * its last resync and moved rigidly by every accepted proposal since; a
+ * rigid motion of the whole chain does not change V, and each move turns
+ * the side of the pivot with fewer residues, so the frame is the chain's
+ * own); after amh_init, amh_energy, or a state change read back,
+ * G(s) built from the torsions in the canonical frame of residue 0 (N at the
+ * origin, CA on +x, C in the xy-plane with y > 0).  Synchronises the stream.
+ */
+amh_status amh_get_coords(amh_ctx* ctx, double* cb_out);
+
+/*
+ * amh_window_coords -- the window coordinates a local sweep scores proposal
+ * k with (Eq. 6: residues floor(k/2) -+ floor(d/2), clipped to the chain),
+ * built from chain `chain`'s current torsions by the local sweep kernel's
+ * own window builder: residue r of [lo, hi] in the canonical frame of
+ * residue lo (as in amh_get_coords).  0 <= window <= 64.
+ *   cb_out  host, double [hi - lo + 1][3].
+ *   lo_out, hi_out  host, the window's first and last residue (may be NULL).
+ * Synchronises the stream.
+ */
+amh_status amh_window_coords(amh_ctx* ctx, int chain, int k, int window, double* cb_out,
+                             int* lo_out, int* hi_out);
 
 /* Text of the last error of ctx (or of the last context-free call). */
 const char* amh_last_error(const amh_ctx* ctx);

@@ -34,7 +34,8 @@ class amh_options(ctypes.Structure):
                 ("lattice_K", ctypes.c_int), ("table_is_neglog", ctypes.c_int),
                 ("stage_table", ctypes.c_int), ("table_texture", ctypes.c_int),
                 ("far_pairs", ctypes.c_int), ("local_chains_per_cta", ctypes.c_int),
-                ("local_threads", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("local_threads", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("keep_coords", ctypes.c_int), ("wait_test", ctypes.c_int)]
 
 
 class amh_trace_rec(ctypes.Structure):
@@ -84,10 +85,12 @@ def load() -> ctypes.CDLL:
     L.amh_exchange.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.c_ulonglong, vp]
     L.amh_grad_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp,
                                    ctypes.c_int, vp, vp, vp]
+    L.amh_get_coords.argtypes = [vp, vp]
+    L.amh_window_coords.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ip, ip]
     for name in ("amh_init", "amh_energy", "amh_sweep", "amh_sweeps", "amh_grad", "amh_get_state",
                  "amh_set_state", "amh_noisy_restart", "amh_get_trace", "amh_counter",
                  "amh_philox", "amh_launch_config", "amh_grad_noalloc", "amh_set_ladder",
-                 "amh_exchange", "amh_pair_terms"):
+                 "amh_exchange", "amh_pair_terms", "amh_get_coords", "amh_window_coords"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -228,6 +231,22 @@ def amh_launch_config(ctx):
     return c.value, t.value, d.value
 
 
+def amh_get_coords(ctx, n_residues_total):
+    """C-beta coordinates of every chain, [sum of L over chains, 3] float64."""
+    out = np.zeros((int(n_residues_total), 3), dtype=np.float64)
+    _check(load().amh_get_coords(ctx, out.ctypes.data), ctx)
+    return out
+
+
+def amh_window_coords(ctx, chain, k, window):
+    """(lo, hi, C-betas [hi-lo+1, 3]) of proposal k's window, in residue lo's frame."""
+    out = np.zeros((int(window) + 1, 3), dtype=np.float64)
+    lo, hi = ctypes.c_int(), ctypes.c_int()
+    _check(load().amh_window_coords(ctx, int(chain), int(k), int(window), out.ctypes.data,
+                                    ctypes.byref(lo), ctypes.byref(hi)), ctx)
+    return lo.value, hi.value, out[:hi.value - lo.value + 1].copy()
+
+
 def amh_last_error(ctx=None) -> str:
     return load().amh_last_error(ctx).decode(errors="replace")
 
@@ -252,4 +271,5 @@ def amh_grad_noalloc(L, B, table, table_is_neglog, edges, theta, batch, E_out, d
 EXPORTED = ["amh_options_default", "amh_init", "amh_energy", "amh_sweep", "amh_sweeps",
             "amh_grad", "amh_get_state", "amh_set_state", "amh_noisy_restart", "amh_get_trace",
             "amh_counter", "amh_philox", "amh_last_error", "amh_launch_config", "amh_destroy",
-            "amh_grad_noalloc", "amh_set_ladder", "amh_exchange", "amh_pair_terms"]
+            "amh_grad_noalloc", "amh_set_ladder", "amh_exchange", "amh_pair_terms",
+            "amh_get_coords", "amh_window_coords"]

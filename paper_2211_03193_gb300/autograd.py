@@ -62,17 +62,25 @@ def lbfgs_refine(sampler, theta0, iterations: int = 500, protein: int = 0, histo
 
 def lbfgs_with_local_mh(sampler, cycles: int, n_lbfgs: int = 80, n_local: int = 20,
                         window: int = 5, T: float = 0.1, sigma_rad: float = 0.07,
-                        seed: int = 1):
+                        seed: int = 1, on_cycle=None):
     """Alternate L-BFGS (n_lbfgs iterations) on every chain of a single-protein
     sampler with n_local localized-MH sweeps (window d), starting from the
-    chains' current states.  Returns the chains' final energies."""
+    chains' current states.  on_cycle(cycle, handed, t0, after), if given,
+    receives the torsions L-BFGS handed to the sampler, the proposal counter
+    the local sweeps started at and the torsions they ended with (host
+    float32 [chains, 2L]).  Returns the chains' final energies."""
     if len(sampler.proteins) != 1:
         raise ValueError("one protein per sampler")
-    n = sampler.proteins[0].n
-    for _ in range(cycles):
-        th = torch.tensor(sampler.torsions(0), device="cuda")
+    # amh_grad takes the context's precision
+    dt = torch.float64 if sampler.precision == 64 else torch.float32
+    for cyc in range(cycles):
+        th = torch.tensor(sampler.torsions(0), device="cuda", dtype=dt)
         th, _ = lbfgs_refine(sampler, th, iterations=n_lbfgs)
         sampler.set_state(th.float().contiguous())
+        if on_cycle is not None:
+            handed, t0 = sampler.torsions(0), sampler.counter(0)
         if n_local:
             sampler.sweeps(_amh.AMH_LOCAL, window, T, sigma_rad, n_local, seed, accepted=False)
+        if on_cycle is not None:
+            on_cycle(cyc, handed, t0, sampler.torsions(0))
     return sampler.energy()

@@ -34,6 +34,7 @@ struct amh_ctx {
   void* best_theta = nullptr;
   float* f32buf = nullptr;  // FP32 staging for precision-64 conversions
   long long* tcount = nullptr;
+  void* coords = nullptr;  // per chain C-betas (keep_coords), precision R
   double* E_cur = nullptr;
   double* best_E = nullptr;
   long long* acc = nullptr;
@@ -74,7 +75,9 @@ thread_local std::string g_free_error;
 amh_status set_err(amh_ctx* ctx, amh_status st, const std::string& m) {
   if (ctx) {
     ctx->msg = m;
-    if (st == AMH_ECUDA) ctx->broken = true;
+    // a device error, or a bounded wait that gave up part-way through a
+    // sweep, leaves the chains' state undefined
+    if (st == AMH_ECUDA || st == AMH_ETIMEOUT) ctx->broken = true;
   } else {
     g_free_error = m;
   }
@@ -148,6 +151,8 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
   a.trace_cap = ctx->opt.trace_capacity;
   a.trace_count = ctx->trace_count;
   a.err = ctx->err;
+  a.coords = (R*)ctx->coords;
+  a.wait_test = ctx->opt.wait_test;
   a.stage_depth = ctx->stage_depth;
   // last bin centre c0 + (B-1) w: beyond it sat(d k1 + k2) = 1 and the FP32
   // term is the constant last entry; 0.01 A covers the rounding of the
@@ -340,7 +345,10 @@ amh_status check_err_flag(amh_ctx* ctx) {
   int h = 0;
   CK(ctx, cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
-  if (h & 2) return set_err(ctx, AMH_ETIMEOUT, "a shared-memory staging wait gave up");
+  if (h & 2) {
+    CK(ctx, cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+    return set_err(ctx, AMH_ETIMEOUT, "a shared-memory staging wait gave up");
+  }
   if (h) return set_err(ctx, AMH_ECUDA, "device reported a non-finite energy");
   return AMH_OK;
 }
@@ -408,6 +416,8 @@ amh_status autotune(amh_ctx* ctx) {
         a.acc_out = nullptr;
         a.trace_chains = 0;
         a.trace_count = nullptr;
+        a.coords = nullptr;
+        a.wait_test = 0;
         a.T = 1.0;
         a.sigma = (R)0.1;
         a.seed = 12345;
@@ -593,7 +603,7 @@ void free_ctx(amh_ctx* ctx) {
   void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
                   ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
                   ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder,
-                  ctx->pair_count};
+                  ctx->pair_count, ctx->coords};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 6; ++q)
@@ -626,6 +636,8 @@ void amh_options_default(amh_options* opt) {
   opt->local_chains_per_cta = 0;
   opt->local_threads = 0;
   opt->stream = nullptr;
+  opt->keep_coords = 0;
+  opt->wait_test = 0;
 }
 
 amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chains_per_protein,
@@ -665,6 +677,9 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
     return set_err(nullptr, AMH_EINVAL, "local_threads must be 0 or a multiple of 32 up to 256");
   if (o.trace_chains < 0 || o.trace_capacity < 0 || o.lattice_K < 0)
     return set_err(nullptr, AMH_EINVAL, "negative option");
+  if (o.keep_coords < 0 || o.keep_coords > 1)
+    return set_err(nullptr, AMH_EINVAL, "keep_coords must be 0 or 1");
+  if (o.wait_test < 0) return set_err(nullptr, AMH_EINVAL, "wait_test must be >= 0");
   // bins: evenly spaced centres
   for (int j = 0; j < B; ++j)
     if (!(edges[j] < edges[j + 1]) || !std::isfinite(edges[j]))
@@ -767,6 +782,11 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   CKI(cudaMemset(ctx->err, 0, sizeof(int)));
   CKI(cudaMalloc(&ctx->pair_count, sizeof(unsigned long long)));
   CKI(cudaMemset(ctx->pair_count, 0, sizeof(unsigned long long)));
+  if (o.keep_coords) {
+    // 3 values per residue per chain: half the torsion count times 3
+    const size_t rs = o.precision == 64 ? sizeof(double) : sizeof(float);
+    CKI(cudaMalloc(&ctx->coords, rs * 3 * (size_t)(ctx->tors_total / 2)));
+  }
   if (o.trace_chains > 0 && o.trace_capacity > 0) {
     const int tc = std::min(o.trace_chains, nc);
     ctx->opt.trace_chains = tc;
@@ -1072,6 +1092,66 @@ amh_status amh_philox(unsigned long long seed, unsigned chain, unsigned long lon
   cudaFree(w);
   cudaFree(z);
   cudaFree(u);
+  return AMH_OK;
+}
+
+amh_status amh_get_coords(amh_ctx* ctx, double* cb_out) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!ctx->coords) return set_err(ctx, AMH_EINVAL, "coordinates are kept only with keep_coords = 1");
+  if (!cb_out) return set_err(ctx, AMH_EINVAL, "cb_out is NULL");
+  st = fresh_energy(ctx);  // a replaced state: G(s) and V are rebuilt together
+  if (st) return st;
+  const size_t cnt = 3 * (size_t)(ctx->tors_total / 2);
+  if (ctx->precision == 64) {
+    CK(ctx, cudaMemcpyAsync(cb_out, ctx->coords, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::vector<float> h(cnt);
+    CK(ctx, cudaMemcpyAsync(h.data(), ctx->coords, sizeof(float) * cnt, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < cnt; ++i) cb_out[i] = (double)h[i];
+  }
+  return check_err_flag(ctx);
+}
+
+amh_status amh_window_coords(amh_ctx* ctx, int chain, int k, int window, double* cb_out,
+                             int* lo_out, int* hi_out) {
+  amh_status st = check_ctx(ctx);
+  if (st) return st;
+  if (chain < 0 || chain >= ctx->total_chains) return set_err(ctx, AMH_EINVAL, "bad chain");
+  if (window < 0 || window > 64) return set_err(ctx, AMH_EINVAL, "window must be in [0, 64]");
+  if (!cb_out) return set_err(ctx, AMH_EINVAL, "cb_out is NULL");
+  int p = 0;
+  while (p + 1 < ctx->nprot && chain >= ctx->prot_h[p + 1].chain0) ++p;
+  const ProteinDev& P = ctx->prot_h[p];
+  if (k < 0 || k >= P.n) return set_err(ctx, AMH_EINVAL, "k must be in [0, 2L)");
+  const int h = window / 2, i = k >> 1;
+  const int lo = std::max(0, i - h), hi = std::min(P.L - 1, i + h);
+  const int cnt = 3 * (hi - lo + 1);
+  const long long off = P.tors0 + (long long)(chain - P.chain0) * P.n;
+  const size_t rs = ctx->precision == 64 ? sizeof(double) : sizeof(float);
+  void* d = nullptr;
+  CK(ctx, cudaMalloc(&d, rs * cnt));
+  cudaError_t e;
+  if (ctx->precision == 64)
+    e = launch_window_coords<double>((const double*)ctx->theta + off, P.L, k, window,
+                                     ideal_geometry<double>(), (double*)d, ctx->stream);
+  else
+    e = launch_window_coords<float>((const float*)ctx->theta + off, P.L, k, window,
+                                    ideal_geometry<float>(), (float*)d, ctx->stream);
+  std::vector<unsigned char> h_(rs * cnt);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_.data(), d, rs * cnt, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "window coordinates");
+  for (int q = 0; q < cnt; ++q)
+    cb_out[q] = ctx->precision == 64 ? ((const double*)h_.data())[q]
+                                     : (double)((const float*)h_.data())[q];
+  if (lo_out) *lo_out = lo;
+  if (hi_out) *hi_out = hi;
   return AMH_OK;
 }
 

@@ -632,6 +632,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity)
   }
   return false;
 }
+// Wait for phase `parity` of an mbarrier with at most `tries` polls (the
+// staging ring's test hook: a wait that is meant to give up).
+__device__ __forceinline__ bool mbar_wait_tries(uint32_t bar, unsigned parity, int tries) {
+  for (int i = 0; i < tries; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
 // Order this thread's earlier generic-proxy accesses of shared memory before
 // later async-proxy (bulk copy) writes to it.
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -606,7 +606,7 @@ __device__ __forceinline__ void cursor_setup(RowCursor& k, int it, int items, in
 template <int C, bool FUSED>
 __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long long tab_off, int L,
                                   int m0, int m1, int f0, int f1, int D, unsigned& par,
-                                  int* err) {
+                                  int* err, int wait_test) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   constexpr int S = 32 / C;
   const int c = lane % C, sl = lane / C;
@@ -625,6 +625,16 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
   const int items = nmg * nch;
   const uint32_t ring = smem_addr(s.ring + (size_t)warp * D * S * RB);
   const uint32_t bar0 = smem_addr(s.bars + (size_t)warp * D);
+  if (wait_test > 0) {
+    // test hook: wait on slot 0 before any copy is issued; nothing can
+    // complete its phase, so the wait gives up with no copy in flight
+    const bool got = mbar_wait_tries(bar0, par & 1u, wait_test);
+    if (!__all_sync(0xffffffffu, got)) {
+      if (lane == 0) atomicOr(err, 2);
+      reduce3f(s, 0.f, 0.f, 0.f);
+      return false;
+    }
+  }
 
   RowCursor F;
   cursor_setup<C>(F, warp, items, nch, m0, m1, f0, f1, L, sl, tab, Bp);
@@ -771,6 +781,23 @@ __device__ void load_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& 
     s.theta[k * C + c] = v;
   }
   if (threadIdx.x < C) s.acc[threadIdx.x] = 0;
+}
+
+// The chain slots' C-betas to the context's coordinate buffer (if kept).
+template <class R, int C>
+__device__ void store_coords(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G,
+                             const ProteinDev& P) {
+  if (!a.coords) return;
+  const int L = P.L;
+  for (int idx = threadIdx.x; idx < L * C; idx += blockDim.x) {
+    const int c = idx / L, i = idx - c * L;
+    if (c >= G.nchains) continue;
+    const long long off = 3 * ((P.tors0 + (long long)(G.chain0 - P.chain0 + c) * P.n) / 2 + i);
+    const V3<R> x = s.cb(i, c);
+    a.coords[off] = x.x;
+    a.coords[off + 1] = x.y;
+    a.coords[off + 2] = x.z;
+  }
 }
 
 // Write back torsions, counters, energies, accepted counts and best states.
@@ -955,9 +982,9 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     if constexpr (ST) {
       const bool ok =
           fused ? pair_block_staged<C, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1,
-                                             a.stage_depth, par, a.err)
+                                             a.stage_depth, par, a.err, a.wait_test)
                 : pair_block_staged<C, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1,
-                                              a.stage_depth, par, a.err);
+                                              a.stage_depth, par, a.err, a.wait_test);
       if (!ok) *(volatile int*)abort_flag = 1;
     } else if constexpr (sizeof(R) == 4) {
       if (a.far_skip) {
@@ -1058,6 +1085,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   } else {
     resync(s, a, P);
   }
+  store_coords(s, a, G, P);
   store_group(s, a, G, P, t0 + steps, true);
   if (a.pair_count && count) atomicAdd(a.pair_count, count);
 }
@@ -1108,6 +1136,7 @@ __global__ void __launch_bounds__(512) energy_kernel(SweepArgs<R> a) {
     const ProteinDev P = a.prot[G.protein];
     load_group(s, a, G, P);
     resync(s, a, P);
+    store_coords(s, a, G, P);
     if (threadIdx.x < C && threadIdx.x < G.nchains) {
       const double e = s.ecur[threadIdx.x];
       if (!(e == e)) atomicOr(a.err, 1);

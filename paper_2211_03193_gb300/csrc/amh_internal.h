@@ -82,6 +82,8 @@ struct SweepArgs {
   long long trace_cap;
   long long* trace_count;  // per traced chain, records written
   int* err;
+  R* coords;      // per chain C-betas, 3 values per residue at 3 * (torsion offset / 2), or null
+  int wait_test;  // staged sweeps: > 0 = first wait on an empty ring slot, this many tries
 };
 
 // Global sweeps (Eqs. 1-3, Alg. 1 first loop) and full-energy resync.
@@ -98,6 +100,13 @@ template <class R, int C, bool ST>
 cudaError_t global_set_smem(size_t bytes);
 template <class R, int C, bool ST>
 cudaError_t global_occupancy(int threads, size_t smem, int* per_sm);
+
+// Window C-betas of proposal k (window d) built by the local sweep kernel's
+// window builder from one chain's torsions (device pointer theta, n values),
+// in the frame of the window's first residue: out[(r - lo) * 3 + xyz].
+template <class R>
+cudaError_t launch_window_coords(const R* theta, int L, int k, int window, Geom<R> geom, R* out,
+                                 cudaStream_t st);
 
 // Local sweeps (Eqs. 4a-b, Eq. 6, Alg. 1 second loop).
 template <class R>

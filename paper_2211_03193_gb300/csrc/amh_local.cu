@@ -71,6 +71,18 @@ __device__ __forceinline__ double local_term<double>(const Tab<double>& tb, long
   return pair_term(tb.E + tab_off + (long long)row * tb.Bp, d, tb);
 }
 
+// The window builder: residue rr of [lo, hi] sits at M_rr = T_{lo+1} o ...
+// o T_rr applied to the canonical residue (the frame of residue lo); Ti(rr)
+// gives T_rr and emit(rr, M_rr) receives each residue's map in order.
+template <class R, class TI, class EMIT>
+__device__ __forceinline__ void window_walk(int lo, int hi, TI Ti, EMIT emit) {
+  Aff<R> M = identity_map<R>();
+  for (int rr = lo; rr <= hi; ++rr) {
+    if (rr > lo) M = compose(M, Ti(rr));
+    emit(rr, M);
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
   extern __shared__ __align__(32) unsigned char smem[];
@@ -142,27 +154,27 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
           const bool scored = p > lo && p <= hi;
           Aff<R> A;  // the move
           if (scored) {
-            // window coordinates: residue rr at M = T_{lo+1} o ... o T_rr
-            // applied to the canonical residue; remember the bond axis
-            Aff<R> M = identity_map<R>();
+            // window coordinates from the cached residue transforms;
+            // remember the bond axis
             V3<R> Pax = cr.N, Qax = cr.CA;
-            for (int rr = lo; rr <= hi; ++rr) {
-              if (rr > lo) M = compose(M, aff_load4(tr_s + ((size_t)rr * Gc + c) * 3));
-              const V3<R> cb = apply(M, cr.CB);
-              const int j = rr - lo;
-              cbs[(j * 3 + 0) * nt + tid] = cb.x;
-              cbs[(j * 3 + 1) * nt + tid] = cb.y;
-              cbs[(j * 3 + 2) * nt + tid] = cb.z;
-              if (rr == i) {
-                if (k & 1) {  // psi_i: CA_i -> C_i
-                  Pax = apply(M, cr.CA);
-                  Qax = apply(M, cr.C);
-                } else {      // phi_i: N_i -> CA_i
-                  Pax = apply(M, cr.N);
-                  Qax = apply(M, cr.CA);
-                }
-              }
-            }
+            window_walk<R>(
+                lo, hi, [&](int rr) { return aff_load4(tr_s + ((size_t)rr * Gc + c) * 3); },
+                [&](int rr, const Aff<R>& M) {
+                  const V3<R> cb = apply(M, cr.CB);
+                  const int j = rr - lo;
+                  cbs[(j * 3 + 0) * nt + tid] = cb.x;
+                  cbs[(j * 3 + 1) * nt + tid] = cb.y;
+                  cbs[(j * 3 + 2) * nt + tid] = cb.z;
+                  if (rr == i) {
+                    if (k & 1) {  // psi_i: CA_i -> C_i
+                      Pax = apply(M, cr.CA);
+                      Qax = apply(M, cr.C);
+                    } else {      // phi_i: N_i -> CA_i
+                      Pax = apply(M, cr.N);
+                      Qax = apply(M, cr.CA);
+                    }
+                  }
+                });
             A = rotation(Pax, Qax, wrap_angle(thn - th));
             for (int b = p; b <= hi; ++b) {
               const int jb = b - lo;
@@ -229,7 +241,44 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
   }
 }
 
+// One window's C-betas by the local kernel's builder (one thread): the
+// residue transforms as the kernel caches them (residue_step of the
+// torsions, stored and loaded through the same 4-value layout), composed
+// by window_walk.
+template <class R>
+__global__ void window_coords_kernel(const R* theta, int L, int k, int window, Geom<R> g,
+                                     R* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const CanonicalResidue<R> cr = canonical_residue(g);
+  const int h = window / 2, i = k >> 1;
+  const int lo = max(0, i - h), hi = min(L - 1, i + h);
+  window_walk<R>(
+      lo, hi,
+      [&](int rr) {
+        Pt4<R> q[3];
+        aff_store4(q, residue_step(g, cr, theta[2 * rr - 1], theta[2 * rr]));
+        return aff_load4(q);
+      },
+      [&](int rr, const Aff<R>& M) {
+        const V3<R> cb = apply(M, cr.CB);
+        out[(rr - lo) * 3 + 0] = cb.x;
+        out[(rr - lo) * 3 + 1] = cb.y;
+        out[(rr - lo) * 3 + 2] = cb.z;
+      });
+}
+
 }  // namespace
+
+template <class R>
+cudaError_t launch_window_coords(const R* theta, int L, int k, int window, Geom<R> geom, R* out,
+                                 cudaStream_t st) {
+  window_coords_kernel<R><<<1, 32, 0, st>>>(theta, L, k, window, geom, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_window_coords<float>(const float*, int, int, int, Geom<float>, float*,
+                                                 cudaStream_t);
+template cudaError_t launch_window_coords<double>(const double*, int, int, int, Geom<double>,
+                                                  double*, cudaStream_t);
 
 template <class R>
 size_t local_smem_bytes(int nmax, int chains_per_cta, int threads, int window) {

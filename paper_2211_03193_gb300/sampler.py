@@ -26,7 +26,7 @@ class Sampler:
                  chains_per_cta: int = 0, threads_per_cta: int = 0, trace_chains: int = 0,
                  trace_capacity: int = 0, lattice_K: int = 0, stage_table: int = 0,
                  table_texture: int = 0, far_pairs: int = 0, local_chains_per_cta: int = 0,
-                 local_threads: int = 0, stream=None):
+                 local_threads: int = 0, keep_coords: int = 0, wait_test: int = 0, stream=None):
         if not isinstance(proteins, (list, tuple)):
             proteins = [proteins]
         chains = list(np.atleast_1d(chains).astype(int))
@@ -58,7 +58,8 @@ class Sampler:
                                        stage_table=stage_table, table_texture=table_texture,
                                        far_pairs=far_pairs,
                                        local_chains_per_cta=local_chains_per_cta,
-                                       local_threads=local_threads, stream=stream)
+                                       local_threads=local_threads, keep_coords=keep_coords,
+                                       wait_test=wait_test, stream=stream)
         self.ctx = _amh.amh_init(np.array(self.L), np.array(chains), torsions, table, edges, opt)
         self.precision = precision
 
@@ -128,6 +129,22 @@ class Sampler:
             dE = torch.empty_like(theta)
         _amh.amh_grad(self.ctx, protein, theta, batch, E_out, dE)
         return E_out, dE
+
+    def coords(self):
+        """C-beta coordinates per chain (needs keep_coords=1): a list over
+        chains of [L, 3] float64 arrays."""
+        X = _amh.amh_get_coords(self.ctx, self.tors_total // 2)
+        out, off = [], 0
+        for p, c in zip(self.proteins, self.chains):
+            for _ in range(c):
+                out.append(X[off:off + p.L])
+                off += p.L
+        return out
+
+    def window_coords(self, chain: int, k: int, window: int):
+        """(lo, hi, C-betas) of the window the local sweep scores proposal k
+        with, built from the chain's current torsions in residue lo's frame."""
+        return _amh.amh_window_coords(self.ctx, chain, k, window)
 
     def pair_terms(self) -> int:
         """Straddle-pair terms the global sweeps have evaluated so far."""

@@ -92,11 +92,64 @@ def test_bench_workload_sampled_parity(amh, orc):
                                        gpu_s0=gst)
                 st = d["s_end"]
                 gst = gpu_advance(gst, seg)
+                print("chain %d sweep %d (%s, T=%.3f): flips %d ties %d max |dE err| %.3g" % (
+                    c, q, "local" if mode == 0 else "global", T, d["flips"], d["ties"],
+                    d["max_dE_err"]))
             assert np.allclose(np.angle(np.exp(1j * (th[c] - st))), 0, atol=1e-4)
     for c in (0, 1, 255, 256, 511, 640, 1022, 1023):
         e = P.energy(th[c].astype(np.float64))
         assert abs(E[c] - e) <= 1e-5 * abs(e), c
         assert bE[c] <= E[c] + 1e-9
+
+
+def test_bench_workload_anneal_tail_parity(amh, orc):
+    """The end of the L=300 / 1024-chain anneal, where the optimisation's
+    decisions are made: every chain runs the whole schedule (333 sweeps, T
+    2.0 -> 0.05, sigma 10 -> 4 deg, Sec. 3's annealing); from the states it
+    ends in, a traced context on the autotuned launch shape runs one more
+    cycle with the parameters of the schedule's last full cycle (T ~ 0.05,
+    sigma ~ 4 deg), and the oracle replays three chains teacher-forced.  No
+    decision may differ from the exact one beyond the contract's 1e-5 tie
+    margin (FP32 rounding flips: none)."""
+    import bench
+    w = bench.workload("amh_L300_c1024")
+    L, n, chains = w["L"], w["n"], w["chains"]
+    prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
+                              seed=w["seed"])
+    tors = synth.random_torsions(chains, L, seed=w["start_seed"])
+    sched = bench.schedule_for(w, seed=1)
+    with amh.Sampler(prot, chains, tors) as s:
+        amh.run_schedule(s, sched)
+        th_end = s.torsions()
+        E_end = s.state()[1]
+    cyc = w["cycle"]
+    last = (sched.total_sweeps // cyc) * cyc - cyc  # first sweep of the last full cycle
+    params = [sched.params(last + q) for q in range(cyc)]
+    assert params[-1][0] == 1 and params[-1][1] < 0.06 and params[-1][2] < math.radians(4.1)
+    stats = []
+    with amh.Sampler(prot, chains, th_end, trace_chains=3, trace_capacity=cyc * n) as s:
+        for mode, T, sigma in params:
+            s.sweeps(mode, w["window"], T, sigma, 1, 77)
+        tr_all = [s.trace(c) for c in range(3)]
+        C = s.launch_config()
+    for c in range(3):
+        tr = tr_all[c]
+        st = gst = th_end[c]
+        for q, (mode, T, sigma) in enumerate(params):
+            seg = tr[q * n:(q + 1) * n]
+            d = replay_and_compare(orc, prot, st, seg, orc.LOCAL if mode == 0 else orc.GLOBAL,
+                                   w["window"], T, sigma, q * n, 77, c, False, gpu_s0=gst)
+            st = d["s_end"]
+            gst = gpu_advance(gst, seg)
+            stats.append((mode, d["flips"], d["ties"], d["max_dE_err"],
+                          float(np.max(d["dE_err"] / np.maximum(d["npairs"], 1)))))
+    flips = sum(x[1] for x in stats)
+    print("anneal tail (T=%.4f, sigma=%.2f deg, launch %r): E_end median %.1f; flips %d, ties %d;"
+          " max |dE err| local %.3g global %.3g; per straddle pair (global) %.3g" % (
+              params[-1][1], math.degrees(params[-1][2]), C, float(np.median(E_end)), flips,
+              sum(x[2] for x in stats), max(x[3] for x in stats if x[0] == 0),
+              max(x[3] for x in stats if x[0] == 1), max(x[4] for x in stats if x[0] == 1)))
+    assert flips == 0
 
 
 def test_uneven_proteins_one_context(amh, orc):

@@ -67,6 +67,109 @@ def test_lbfgs_with_local_mh_runs_and_improves(env):
         assert s.counter(0) == 2 * 2 * 2 * L  # two cycles of two local sweeps
 
 
+def _wrapped_close(a, b, atol):
+    return np.all(np.abs(np.angle(np.exp(1j * (np.asarray(a, np.float64) - b)))) <= atol)
+
+
+def test_lbfgs_with_local_mh_local_phase_equals_oracle(env, orc):
+    """Sec. 3's L-BFGS with localized MH, FP64 form: after every L-BFGS phase
+    the oracle replays the localized-MH sweeps from exactly the state L-BFGS
+    handed over (the same counter, seed, window, T and sigma) and must end at
+    the GPU's torsions; the energies the driver returns are the oracle's V of
+    the final torsions."""
+    torch, sampler, autograd = env
+    L, chains = 28, 4
+    n = 2 * L
+    prot = synth.make_protein(L, seed=825)
+    tors = synth.random_torsions(chains, L, seed=826)
+    P = orc.Problem(L, prot.p, prot.edges)
+    T, sigma, window, n_local, seed = 0.2, 0.07, 5, 3, 9
+    seen = []
+
+    def on_cycle(cyc, handed, t0, after):
+        seen.append((handed.copy(), t0, after.copy()))
+
+    with sampler.Sampler(prot, chains, tors, precision=64) as s:
+        E = autograd.lbfgs_with_local_mh(s, cycles=3, n_lbfgs=15, n_local=n_local,
+                                         window=window, T=T, sigma_rad=sigma, seed=seed,
+                                         on_cycle=on_cycle)
+        th_end = s.torsions()
+    assert len(seen) == 3
+    for cyc, (handed, t0, after) in enumerate(seen):
+        assert t0 == cyc * n_local * n
+        if cyc:  # L-BFGS started from the previous cycle's end state
+            assert not np.array_equal(handed, seen[cyc - 1][2])
+        for c in range(chains):
+            st, _, tr = P.run(handed[c].astype(np.float64), orc.LOCAL, window, T, sigma, t0,
+                              n_local * n, seed, c, trace=True)
+            # FP64 GPU form: only a near-tie (|ln u + dV/T| < 1e-5) could part
+            # the paths; none occurs in this run
+            margin = np.abs(tr["lnu"] + tr["dV"] / T)
+            assert margin.min() >= 1e-5
+            assert _wrapped_close(after[c], st, 1e-6), (cyc, c)
+    for c in range(chains):
+        assert abs(E[c] - P.energy(th_end[c].astype(np.float64))) <= 1e-10 * abs(E[c])
+
+
+def test_restart_from_best_equals_oracle(env, orc):
+    """Sec. 2.3's restarts, FP64 form: the oracle replays every run from the
+    best state the previous runs reached (kept at global-sweep ends, strictly
+    lower energy), with the run's seed and its sigma range (10 -> 4 deg while
+    runs improve the lowest energy over the chains, 10/F -> 1/F deg after F
+    runs that did not), and must reach the GPU's torsions, best energies and
+    sigma ranges run by run."""
+    import dataclasses
+    torch, sampler, autograd = env
+    L, chains = 20, 6
+    n = 2 * L
+    prot = synth.make_protein(L, seed=855)
+    tors = synth.random_torsions(chains, L, seed=856)
+    sched = sampler.Schedule(total_sweeps=11, n_local=10, n_global=1, window=8, T0=0.6, T1=0.1,
+                             seed=5)
+    runs = 5
+    P = orc.Problem(L, prot.p, prot.edges)
+    gpu = []
+    with sampler.Sampler(prot, chains, tors, precision=64) as s:
+        sampler.restart_from_best(
+            s, sched, runs=runs,
+            on_run=lambda r, b, sig: gpu.append((sig, b) + tuple(np.copy(v) for v in s.state())))
+    S = tors.astype(np.float64)
+    bestE = P.energies(S)
+    bestS = S.copy()
+    best_all = float(bestE.min())
+    failures = 0
+    for r in range(runs):
+        sig = (10.0 / failures, 1.0 / failures) if failures else (10.0, 4.0)
+        sig_gpu, b_gpu, th, E, bE, bt = gpu[r]
+        assert sig_gpu == sig, (r, sig_gpu, sig)
+        sr = dataclasses.replace(sched, sigma0_deg=sig[0], sigma1_deg=sig[1],
+                                 seed=sched.seed + 7919 * r)
+        if r:  # every chain from its best state, through the FP32 interface
+            S = bestS.astype(np.float32).astype(np.float64)
+        for q in range(sched.total_sweeps):
+            mode, T, sigma = sr.params(q)
+            t0 = (r * sched.total_sweeps + q) * n
+            S, _ = P.run_chains(S, orc.LOCAL if mode == 0 else orc.GLOBAL, sr.window_of(q), T,
+                                sigma, t0, n, sr.seed, 0)
+            if mode == 1:
+                Eq = P.energies(S)
+                better = Eq < bestE
+                bestE[better] = Eq[better]
+                bestS[better] = S[better]
+        th = th.reshape(chains, n)
+        bt = bt.reshape(chains, n)
+        for c in range(chains):
+            assert _wrapped_close(th[c], S[c], 1e-6), (r, c)
+            assert _wrapped_close(bt[c], bestS[c], 1e-6), (r, c)
+        assert np.allclose(bE, bestE, rtol=1e-10, atol=0), (r, bE - bestE)
+        now = float(bestE.min())
+        if now < best_all:
+            best_all = now
+        else:
+            failures += 1
+        assert abs(b_gpu - best_all) <= 1e-10 * abs(best_all)
+
+
 @pytest.mark.parametrize("noisy", [0, 3])
 def test_graph_replay_equals_eager_schedule(env, noisy):
     torch, sampler, autograd = env

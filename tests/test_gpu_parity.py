@@ -126,18 +126,36 @@ def replay_and_compare(orc, prot, s0, tr, mode, window, T, sigma, t0, seed, chai
     else:
         tol = de_tol(npairs, exact, reach_of(prot))
         lnu_tol = 2e-6
-    assert np.all(np.abs(tr["lnu"] - otr["lnu"]) <= lnu_tol * (1 + np.abs(otr["lnu"])))
+    lnu_err = np.abs(tr["lnu"] - otr["lnu"])
+    assert np.all(lnu_err <= lnu_tol * (1 + np.abs(otr["lnu"])))
     th_err = np.abs(np.angle(np.exp(1j * (tr["theta_new"] - otr["theta_new"]))))
     assert np.all(th_err <= (1e-12 if fp64 else 2e-6)), th_err.max()
     bad = dE_err > tol
     assert not bad.any(), (np.flatnonzero(bad)[:5], dE_err[bad][:5],
                            tol[bad][:5] if np.ndim(tol) else tol, exact[bad][:5],
                            npairs[bad][:5] if np.ndim(npairs) else npairs)
+    # every GPU decision follows Eq. 1 from the GPU's own ln u and Delta-E,
+    # in the precision the kernel decides in (FP32 local sweeps: FP32; the
+    # rest: FP64 products of the stored values)
+    if not fp64 and mode == orc.LOCAL:
+        own = (tr["lnu"].astype(np.float32) * np.float32(T)) < -tr["dE"].astype(np.float32)
+    else:
+        own = tr["lnu"] * T < -tr["dE"]
+    assert np.array_equal(tr["accept"].astype(bool), own), np.flatnonzero(tr["accept"] != own)[:5]
+    # so a decision can differ from the exact one (the oracle's ln u and the
+    # FP64 Delta-E) only within the measured error of those two values: a
+    # disagreement is a tie (margin < 1e-5, the contract's allowance) or an
+    # FP32 rounding flip (margin below this step's |Delta-E error| / T plus
+    # its ln u error); anything else fails
     margin = np.abs(otr["lnu"] + exact / T)
     disagree = tr["accept"] != (otr["lnu"] * T < -exact)
-    allowed = margin <= (tol / T + 1e-5)
-    assert np.all(allowed[disagree]), (np.flatnonzero(disagree & ~allowed)[:5])
-    return dict(max_dE_err=float(dE_err.max()), disagree=int(disagree.sum()), n=steps,
+    tie = margin < 1e-5
+    explained = margin <= dE_err / T + lnu_err + 1e-12
+    assert np.all((tie | explained)[disagree]), np.flatnonzero(disagree & ~(tie | explained))[:5]
+    flips = disagree & ~tie
+    return dict(max_dE_err=float(dE_err.max()), disagree=int(disagree.sum()),
+                ties=int((disagree & tie).sum()), flips=int(flips.sum()), n=steps,
+                dE_err=dE_err, npairs=npairs, exact=exact, margin=margin,
                 s_end=s_end, gpu_s_end=gpu_end,
                 replay_dE_gap=float(np.max(np.abs(otr["dV"] - exact), initial=0.0)))
 
