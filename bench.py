@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--local-threads", type=int, default=0, help="local-sweep threads per CTA")
     ap.add_argument("--stage", type=int, default=0,
                     help="table rows: 0 tuned, 1 staged in shared memory, 2 through L1")
+    ap.add_argument("--global-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="global sweeps: 0 tuned, 1 chains of a CTA in lock-step, "
+                         "2 one warp per chain")
     ap.add_argument("--clocks-csv", default="",
                     help="keep the nvidia-smi clock samples of the timed region in this file "
                          "(default: a temporary file, removed after it is summarised)")
@@ -431,7 +434,7 @@ def run_batched():
             e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        C, thr, D = s.launch_config()
+        C, thr, D, K = s.launch_config()
     props = sum(11 * 2 * L * w["chains"] for L in Ls)
     print(json.dumps({"experiment": "batched", "proteins": len(Ls), "chains": sum(chains),
                       "L_range": [min(Ls), max(Ls)], "ms_per_cycle": ms,
@@ -586,11 +589,12 @@ def run_ours(args):
     samp = Sampler(prot, chains, tors, precision=w["precision"], stream=stream,
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
                    stage_table=args.stage, table_texture=args.texture, far_pairs=args.far_pairs,
-                   local_chains_per_cta=args.local_chains_per_cta, local_threads=args.local_threads)
+                   local_chains_per_cta=args.local_chains_per_cta, local_threads=args.local_threads,
+                   global_kernel=args.global_kernel)
     # a context for the gradient pass only (fixed launch shape: no autotuning)
     gsamp = Sampler(prot, 1, tors[:1], precision=w["precision"], stream=aux, chains_per_cta=1,
                     threads_per_cta=128)
-    C, thr, D = samp.launch_config()
+    C, thr, D, K = samp.launch_config()
     # device table: one 8-byte entry per bin, rows padded to an even bin count
     B = len(synth.edges_by_name(w["bins"])) - 1
     tab_mb = (L * (L - 1) // 2) * ((B + 1) & ~1) * (8 if w["precision"] == 32 else 16) / 1e6

@@ -108,6 +108,15 @@ typedef struct {
                               tries.  Nothing can arrive there, so the wait
                               gives up with no copy in flight and the call
                               fails with AMH_ETIMEOUT. */
+  int global_kernel;       /* global sweeps: 0 = chosen by the autotuner among
+                              both kernels (the CTA kernel if chains_per_cta is
+                              set); 1 = the CTA kernel (chains_per_cta chains
+                              of a CTA in lock-step); 2 = one warp per chain
+                              (chains_per_cta = chains, i.e. warps, per CTA:
+                              0 = tuned, 1, 2, 4 or 8), which needs precision
+                              32, the far-field skip (far_pairs 0, L <= 768)
+                              and no staging, else AMH_EINVAL.  Both kernels
+                              compute the same proposals and decisions. */
 } amh_options;
 
 /* One proposal record (traced chains only), 32 bytes. */
@@ -317,9 +326,11 @@ amh_status amh_window_coords(amh_ctx* ctx, int chain, int k, int window, double*
 const char* amh_last_error(const amh_ctx* ctx);
 
 /* Launch shape of the global sweeps (after tuning): chains per CTA, threads
- * per CTA and staging-ring depth (0 = table rows read through L1). */
+ * per CTA, staging-ring depth (0 = table rows read through L1) and kernel
+ * (1 = chains of a CTA in lock-step, 2 = one warp per chain); any pointer
+ * may be NULL. */
 amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta,
-                             int* stage_depth);
+                             int* stage_depth, int* kernel);
 
 /* Free everything the context owns.  NULL is ignored. */
 void amh_destroy(amh_ctx* ctx);

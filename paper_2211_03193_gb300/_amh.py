@@ -35,7 +35,8 @@ class amh_options(ctypes.Structure):
                 ("stage_table", ctypes.c_int), ("table_texture", ctypes.c_int),
                 ("far_pairs", ctypes.c_int), ("local_chains_per_cta", ctypes.c_int),
                 ("local_threads", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("keep_coords", ctypes.c_int), ("wait_test", ctypes.c_int)]
+                ("keep_coords", ctypes.c_int), ("wait_test", ctypes.c_int),
+                ("global_kernel", ctypes.c_int)]
 
 
 class amh_trace_rec(ctypes.Structure):
@@ -78,7 +79,7 @@ def load() -> ctypes.CDLL:
                              ctypes.c_longlong, vp, vp, vp]
     L.amh_last_error.argtypes = [vp]
     L.amh_last_error.restype = ctypes.c_char_p
-    L.amh_launch_config.argtypes = [vp, ip, ip, ip]
+    L.amh_launch_config.argtypes = [vp, ip, ip, ip, ip]
     L.amh_destroy.argtypes = [vp]
     L.amh_destroy.restype = None
     L.amh_set_ladder.argtypes = [vp, ctypes.c_int, vp]
@@ -226,9 +227,12 @@ def amh_philox(seed, chain, t0, stream, count):
 
 
 def amh_launch_config(ctx):
-    c, t, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load().amh_launch_config(ctx, ctypes.byref(c), ctypes.byref(t), ctypes.byref(d)), ctx)
-    return c.value, t.value, d.value
+    """(chains per CTA, threads per CTA, staging depth, kernel: 1 CTA lock-step,
+    2 warp per chain) of the global sweeps."""
+    c, t, d, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().amh_launch_config(ctx, ctypes.byref(c), ctypes.byref(t), ctypes.byref(d),
+                                    ctypes.byref(k)), ctx)
+    return c.value, t.value, d.value, k.value
 
 
 def amh_get_coords(ctx, n_residues_total):

@@ -21,7 +21,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libamh.so")
 PEAKS_LIB = os.path.join(PKG, "libamh_peaks.so")
 
-SOURCES = ["amh_api.cu", "amh_global.cu", "amh_local.cu", "amh_misc.cu", "amh_noalloc.cu"]
+SOURCES = ["amh_api.cu", "amh_global.cu", "amh_gwarp.cu", "amh_local.cu", "amh_misc.cu",
+           "amh_noalloc.cu"]
 PEAKS_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

@@ -51,6 +51,11 @@ struct amh_ctx {
   long long* trace_count = nullptr;
   // launch configuration
   int C = 8, threads = 256, grid_global = 1;
+  // one warp per chain (FP32 far-field kernel): chains (warps) per CTA and grid
+  bool use_warp = false;
+  int warpW = 4, grid_warp = 1;
+  GroupDev* wgroups_d = nullptr;  // one chain per group
+  int nwgroups = 0;
   int stage_depth = 0;  // > 0: global sweeps stage table rows through shared memory
   cudaTextureObject_t tex = 0;  // FP32 table as a 1-D texture (0: not used)
   double* ladder = nullptr;  // parallel tempering: per-slot temperature factors
@@ -325,6 +330,29 @@ amh_status configure_global(amh_ctx* ctx, int C, int threads, int D) {
   return AMH_OK;
 }
 
+// The warp-per-chain kernel applies to FP32 sweeps that skip the far field
+// (chunk bits of L <= 64 chunks) without staging.
+bool warp_applies(const amh_ctx* ctx) {
+  return ctx->precision == 32 && ctx->opt.far_pairs == 0 && ctx->opt.stage_table != 1 &&
+         ctx->Lmax <= kMaxChunks * kPairChunk && ctx->opt.global_kernel != 1;
+}
+
+amh_status configure_warp(amh_ctx* ctx, int W) {
+  const size_t sm = gwarp_smem_bytes(ctx->Lmax, W);
+  if (sm > ctx->smem_optin - kStaticSmemMargin)
+    return set_err(ctx, AMH_EINVAL, "shared memory for this many chains per CTA does not fit");
+  if (!ctx->wgroups_d) {
+    amh_status st = upload_groups(ctx, make_groups(ctx, 1), &ctx->wgroups_d, &ctx->nwgroups);
+    if (st) return st;
+  }
+  int per_sm = 1;
+  CK(ctx, gwarp_occupancy(W, sm, &per_sm));
+  ctx->warpW = W;
+  const int ctas = (ctx->nwgroups + W - 1) / W;
+  ctx->grid_warp = std::max(1, std::min(ctas, ctx->sm_count * std::max(per_sm, 1)));
+  return AMH_OK;
+}
+
 template <class R>
 amh_status run_energy(amh_ctx* ctx) {
   SweepArgs<R> a = make_args<R>(ctx);
@@ -372,7 +400,7 @@ amh_status autotune(amh_ctx* ctx) {
   cudaEvent_t e0, e1;
   CK(ctx, cudaEventCreate(&e0));
   CK(ctx, cudaEventCreate(&e1));
-  float best_ms = 1e30f;
+  float best_ms = 1e30f, last_ms = 0.f;
   int bestC = 0, bestT = 256, bestD = 0;
   // three runs of up to 64 proposals, at 1/6, 1/2 and 5/6 of each sweep:
   // the straddle blocks there have the sizes a whole sweep averages over
@@ -386,8 +414,71 @@ amh_status autotune(amh_ctx* ctx) {
       for (int c = 0; c < ctx->nch[p]; ++c) tstart[seg][ctx->prot_h[p].chain0 + c] = at;
     }
   }
+  // the warp-per-chain kernel: chains (warps) per CTA
+  int bestW = 0;
+  float best_warp_ms = 1e30f;
+  auto time_runs = [&](auto launch) -> amh_status {
+    float ms_sum = 0.f;
+    for (int run = 0; run < 4; ++run) {  // run 0 warms up, runs 1-3 are timed
+      const int seg = run == 0 ? 1 : run - 1;
+      CK(ctx, cudaMemcpyAsync(th_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(ctx, cudaMemcpyAsync(bt_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(ctx, cudaMemcpyAsync(t_scr, tstart[seg].data(), sizeof(long long) * ctx->total_chains,
+                              cudaMemcpyHostToDevice, ctx->stream));
+      CK(ctx, cudaMemsetAsync(be_scr, 0x7f, sizeof(double) * ctx->total_chains, ctx->stream));
+      SweepArgs<R> a = make_args<R>(ctx);
+      a.theta = th_scr;
+      a.best_theta = bt_scr;
+      a.tcount = t_scr;
+      a.E_cur = e_scr;
+      a.best_E = be_scr;
+      a.acc_out = nullptr;
+      a.trace_chains = 0;
+      a.trace_count = nullptr;
+      a.coords = nullptr;
+      a.wait_test = 0;
+      a.pair_count = nullptr;
+      a.T = 1.0;
+      a.sigma = (R)0.1;
+      a.seed = 12345;
+      a.steps = steps;
+      a.resync_every = 1 << 30;
+      CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
+      CK(ctx, cudaEventRecord(e0, ctx->stream));
+      CK(ctx, launch(a));
+      CK(ctx, cudaEventRecord(e1, ctx->stream));
+      CK(ctx, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (run) ms_sum += ms;
+    }
+    last_ms = ms_sum;
+    return AMH_OK;
+  };
+  if constexpr (sizeof(R) == 4) {
+    if (warp_applies(ctx)) {
+      const int candW[4] = {1, 2, 4, 8};
+      for (int W : candW) {
+        if (gwarp_smem_bytes(ctx->Lmax, W) > ctx->smem_optin - kStaticSmemMargin) continue;
+        amh_status st = configure_warp(ctx, W);
+        if (st) return st;
+        st = time_runs([&](const SweepArgs<R>& a0) {
+          SweepArgs<R> a = a0;
+          a.groups = ctx->wgroups_d;
+          a.ngroups = ctx->nwgroups;
+          return launch_gwarp(a, W, ctx->grid_warp, ctx->stream);
+        });
+        if (st) return st;
+        if (last_ms < best_warp_ms) {
+          best_warp_ms = last_ms;
+          bestW = W;
+        }
+      }
+    }
+  }
   for (int C : cand_C) {
     if (C > max_C(ctx->precision)) continue;
+    if (ctx->opt.global_kernel == 2) break;  // the CTA kernel only serves energies
     for (int T : cand_T) {
      for (int staged = 0; staged < 2; ++staged) {
       if (staged && (ctx->opt.stage_table == 2 || T < 256)) continue;
@@ -399,39 +490,11 @@ amh_status autotune(amh_ctx* ctx) {
         continue;
       amh_status st = configure_global<R>(ctx, C, T, D);
       if (st) return st;
-      float ms_sum = 0.f;
-      for (int run = 0; run < 4; ++run) {  // run 0 warms up, runs 1-3 are timed
-        const int seg = run == 0 ? 1 : run - 1;
-        CK(ctx, cudaMemcpyAsync(th_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(ctx, cudaMemcpyAsync(bt_scr, ctx->theta, tb, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(ctx, cudaMemcpyAsync(t_scr, tstart[seg].data(), sizeof(long long) * ctx->total_chains,
-                                cudaMemcpyHostToDevice, ctx->stream));
-        CK(ctx, cudaMemsetAsync(be_scr, 0x7f, sizeof(double) * ctx->total_chains, ctx->stream));
-        SweepArgs<R> a = make_args<R>(ctx);
-        a.theta = th_scr;
-        a.best_theta = bt_scr;
-        a.tcount = t_scr;
-        a.E_cur = e_scr;
-        a.best_E = be_scr;
-        a.acc_out = nullptr;
-        a.trace_chains = 0;
-        a.trace_count = nullptr;
-        a.coords = nullptr;
-        a.wait_test = 0;
-        a.T = 1.0;
-        a.sigma = (R)0.1;
-        a.seed = 12345;
-        a.steps = steps;
-        a.resync_every = 1 << 30;
-        CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
-        CK(ctx, cudaEventRecord(e0, ctx->stream));
-        CK(ctx, glaunch<R>(false, C, D > 0, a, T, ctx->grid_global, ctx->stream));
-        CK(ctx, cudaEventRecord(e1, ctx->stream));
-        CK(ctx, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
-        if (run) ms_sum += ms;
-      }
+      st = time_runs([&](const SweepArgs<R>& a) {
+        return glaunch<R>(false, C, D > 0, a, T, ctx->grid_global, ctx->stream);
+      });
+      if (st) return st;
+      const float ms_sum = last_ms;
       if (ms_sum < best_ms) {
         best_ms = ms_sum;
         bestC = C;
@@ -448,9 +511,21 @@ amh_status autotune(amh_ctx* ctx) {
   cudaFree(bt_scr);
   cudaFree(e_scr);
   cudaFree(be_scr);
-  if (!bestC) return set_err(ctx, AMH_EINVAL, "no launch shape fits in shared memory");
   amh_status st = check_err_flag(ctx);
   if (st) return st;
+  if (bestW && (best_warp_ms <= best_ms || ctx->opt.global_kernel == 2)) {
+    st = configure_warp(ctx, bestW);
+    if (st) return st;
+    ctx->use_warp = true;
+    // energies (and a precision-64 or staged request) still use the CTA kernel
+    if (!bestC) {
+      bestC = 1;
+      bestT = 128;
+    }
+  } else if (ctx->opt.global_kernel == 2) {
+    return set_err(ctx, AMH_EINVAL, "the warp-per-chain kernel does not fit in shared memory");
+  }
+  if (!bestC) return set_err(ctx, AMH_EINVAL, "no launch shape fits in shared memory");
   return configure_global<R>(ctx, bestC, bestT, bestD);
 }
 
@@ -495,12 +570,20 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   CK(ctx, launch_convert_in<R>(ctx->f32buf, (R*)ctx->theta, ctx->tors_total, ctx->stream));
   // kernels may use all of the opt-in shared memory
   for (int C = 1; C <= max_C(ctx->precision); C *= 2) CK(ctx, gset<R>(C, ctx->smem_optin));
+  if (ctx->precision == 32) CK(ctx, gwarp_set_smem(ctx->smem_optin));
+  if (ctx->opt.global_kernel == 2 && !warp_applies(ctx))
+    return set_err(ctx, AMH_EINVAL, "the warp-per-chain kernel needs L <= 768");
   CK(ctx, local_set_smem<R>(ctx->smem_optin));
   CK(ctx, grad_set_smem<R>(ctx->smem_optin));
   // launch shape
   amh_status st;
   if (ctx->opt.chains_per_cta == 0) {
     st = autotune<R>(ctx);
+  } else if (ctx->opt.global_kernel == 2) {
+    st = configure_warp(ctx, ctx->opt.chains_per_cta);
+    if (st) return st;
+    ctx->use_warp = true;
+    st = configure_global<R>(ctx, 1, 128, 0);  // the energy kernel's shape
   } else {
     const int C = ctx->opt.chains_per_cta;
     const int T = ctx->opt.threads_per_cta ? ctx->opt.threads_per_cta : 256;
@@ -543,6 +626,14 @@ amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma
   a.window = window;
   CK(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(int), ctx->stream));
   if (mode == AMH_GLOBAL) {
+    if constexpr (sizeof(R) == 4) {
+      if (ctx->use_warp) {
+        a.groups = ctx->wgroups_d;
+        a.ngroups = ctx->nwgroups;
+        CK(ctx, launch_gwarp(a, ctx->warpW, ctx->grid_warp, ctx->stream));
+        return AMH_OK;
+      }
+    }
     CK(ctx, glaunch<R>(false, ctx->C, ctx->stage_depth > 0, a, ctx->threads, ctx->grid_global,
                        ctx->stream));
   } else {
@@ -603,7 +694,7 @@ void free_ctx(amh_ctx* ctx) {
   void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
                   ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
                   ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder,
-                  ctx->pair_count, ctx->coords};
+                  ctx->pair_count, ctx->coords, ctx->wgroups_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 6; ++q)
@@ -638,6 +729,7 @@ void amh_options_default(amh_options* opt) {
   opt->stream = nullptr;
   opt->keep_coords = 0;
   opt->wait_test = 0;
+  opt->global_kernel = 0;
 }
 
 amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chains_per_protein,
@@ -680,6 +772,13 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   if (o.keep_coords < 0 || o.keep_coords > 1)
     return set_err(nullptr, AMH_EINVAL, "keep_coords must be 0 or 1");
   if (o.wait_test < 0) return set_err(nullptr, AMH_EINVAL, "wait_test must be >= 0");
+  if (o.global_kernel < 0 || o.global_kernel > 2)
+    return set_err(nullptr, AMH_EINVAL, "global_kernel must be 0, 1 or 2");
+  if (o.global_kernel == 2 &&
+      (o.precision != 32 || o.far_pairs != 0 || o.stage_table == 1 || o.threads_per_cta != 0))
+    return set_err(nullptr, AMH_EINVAL,
+                   "the warp-per-chain kernel needs precision 32, far_pairs 0, no staging and no "
+                   "threads_per_cta");
   // bins: evenly spaced centres
   for (int j = 0; j < B; ++j)
     if (!(edges[j] < edges[j + 1]) || !std::isfinite(edges[j]))
@@ -1160,11 +1259,12 @@ const char* amh_last_error(const amh_ctx* ctx) {
 }
 
 amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta,
-                             int* stage_depth) {
+                             int* stage_depth, int* kernel) {
   if (!ctx) return AMH_ESTATE;
-  if (chains_per_cta) *chains_per_cta = ctx->C;
-  if (threads_per_cta) *threads_per_cta = ctx->threads;
-  if (stage_depth) *stage_depth = ctx->stage_depth;
+  if (chains_per_cta) *chains_per_cta = ctx->use_warp ? ctx->warpW : ctx->C;
+  if (threads_per_cta) *threads_per_cta = ctx->use_warp ? 32 * ctx->warpW : ctx->threads;
+  if (stage_depth) *stage_depth = ctx->use_warp ? 0 : ctx->stage_depth;
+  if (kernel) *kernel = ctx->use_warp ? 2 : 1;
   return AMH_OK;
 }
 

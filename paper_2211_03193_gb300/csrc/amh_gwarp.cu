@@ -1,0 +1,658 @@
+// amh_gwarp.cu -- global Metropolis sweeps (Eqs. 1-3, Alg. 1 first loop),
+// one warp per chain, FP32 with the flat far field skipped.
+//
+// Each warp takes chains from the work queue and runs a chain's proposals
+// on its own: every step is warp-synchronous (shuffles and __syncwarp, no
+// CTA barrier), so a warp waiting on a map, a sphere or a table fetch holds
+// up nothing but itself and the SM issues the other warps' work meanwhile.
+// A CTA is only a set of such warps sharing the residue-transform basis.
+//
+// Per proposal (the pair 2i-1, 2i = psi_{i-1}, phi_i shares the pivot
+// p = i and is scored in one pass, as in the CTA kernel): lanes 0-2 form
+// the rigid maps A1, A2 and A21 of the moving side (the side of the pivot
+// with fewer residues, Sec. 2.4 step 2); the fixed side's C-betas are cut
+// into absolute chunks of kPairChunk atoms with bounding spheres; each lane
+// takes moving atoms and tests their images' sphere against every chunk;
+// the (moving atom, chunk) items whose spheres come within the last bin
+// centre (plus a rounding margin) are listed and run through the pair loop
+// of Eq. 5, the rest add exactly zero (their terms are the flat last bin
+// before and after the move).  The Metropolis test of Eq. 1 is taken by
+// every lane alike from the warp's butterfly sums.
+//
+// Chunk spheres are kept across proposals: chunk j remembers the atom range
+// [lo, hi) that has not moved since its sphere was computed (a commit of the
+// moving side [m0, m1) removes that range), and a sphere is recomputed only
+// when a proposal's fixed part of the chunk is not inside it.  Within a
+// sweep the fixed side is [p, L) while p <= L/2 and [0, p) after, so most
+// spheres are computed once or twice per sweep.
+#include "amh_internal.h"
+
+namespace amh {
+
+namespace {
+
+constexpr int kWC = kPairChunk;  // C-betas per chunk: chunk j holds atoms [kWC j, kWC j + kWC)
+constexpr int kWDraw = 64;       // proposals whose draws are made ahead
+constexpr size_t kKbBytes = 1792;  // residue-transform basis: 216 doubles, 128-byte rounded
+
+__host__ __device__ inline size_t wal(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Shared memory of one warp (one chain of up to Lmax residues).
+struct WLayout {
+  size_t cb, fsph, maps, theta, bb, draws, clean, list, total;
+  int nJ, cap;
+  __host__ __device__ explicit WLayout(int Lmax) {
+    nJ = (Lmax + kWC - 1) / kWC;
+    cap = 32 * nJ + 32;  // items of one round of 32 moving atoms plus a partial batch
+    size_t o = 0;
+    cb = o;    o = wal(o + sizeof(Pt4<float>) * (size_t)Lmax);
+    fsph = o;  o = wal(o + sizeof(Pt4<float>) * (size_t)nJ);
+    maps = o;  o = wal(o + sizeof(float) * 40);
+    theta = o; o = wal(o + sizeof(float) * 2 * (size_t)Lmax);
+    bb = o;    o = wal(o + sizeof(float) * 9 * (size_t)Lmax);
+    draws = o; o = wal(o + sizeof(float) * 2 * kWDraw);
+    clean = o; o = wal(o + sizeof(int) * (size_t)nJ);
+    list = o;  o = wal(o + sizeof(unsigned short) * (size_t)cap);
+    total = (o + 127) & ~size_t(127);
+  }
+};
+
+struct WShm {
+  Pt4<float>* cb;        // [L] C-betas (x, y, z, 0)
+  Pt4<float>* fsph;      // [chunk] bounding sphere (centre, radius)
+  float* maps;           // A1 [0,12), A2 [12,24), A21 [24,36); thn [36,38), ln u [38,40)
+  float* theta;          // [n]
+  float* bb;             // [i][v][xyz]: v 0 CA_i, 1 unit N_i -> CA_i, 2 unit CA_i -> C_i
+  float* draws;          // [kWDraw][2]: (z, ln u)
+  int* clean;            // [chunk] lo | hi << 16: atoms unmoved since the sphere was made
+  unsigned short* list;  // items (moving atom << 6 | chunk)
+  __device__ WShm(unsigned char* base, const WLayout& l) {
+    cb = (Pt4<float>*)(base + l.cb);
+    fsph = (Pt4<float>*)(base + l.fsph);
+    maps = (float*)(base + l.maps);
+    theta = (float*)(base + l.theta);
+    bb = (float*)(base + l.bb);
+    draws = (float*)(base + l.draws);
+    clean = (int*)(base + l.clean);
+    list = (unsigned short*)(base + l.list);
+  }
+  __device__ V3<float> x(int i) const {
+    const Pt4<float> p = cb[i];
+    return v3<float>(p.x, p.y, p.z);
+  }
+  __device__ void set_x(int i, V3<float> v) {
+    Pt4<float> p;
+    p.x = v.x;
+    p.y = v.y;
+    p.z = v.z;
+    p.w = 0.f;
+    cb[i] = p;
+  }
+  __device__ V3<float> axis(int i, int v) const {
+    const float* q = bb + i * 9 + v * 3;
+    return v3<float>(q[0], q[1], q[2]);
+  }
+  __device__ void set_axis(int i, int v, V3<float> a) {
+    float* q = bb + i * 9 + v * 3;
+    q[0] = a.x;
+    q[1] = a.y;
+    q[2] = a.z;
+  }
+};
+
+// --- moves (the same arithmetic as the CTA kernel's: y = q + M (x - p)) ---
+struct WMove {
+  float m[9];
+  float p[3];
+  float q[3];
+};
+
+__device__ __forceinline__ WMove wmove_rotation(V3<float> P, V3<float> u, float ang) {
+  const Aff<float> A = rotation_axis(P, u, ang);
+  WMove M;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) M.m[i] = A.m[i];
+  M.p[0] = M.q[0] = P.x;
+  M.p[1] = M.q[1] = P.y;
+  M.p[2] = M.q[2] = P.z;
+  return M;
+}
+__device__ __forceinline__ V3<float> wmove_lin(const WMove& A, V3<float> v) {
+  return v3<float>(fmaf(A.m[0], v.x, fmaf(A.m[1], v.y, A.m[2] * v.z)),
+                   fmaf(A.m[3], v.x, fmaf(A.m[4], v.y, A.m[5] * v.z)),
+                   fmaf(A.m[6], v.x, fmaf(A.m[7], v.y, A.m[8] * v.z)));
+}
+__device__ __forceinline__ V3<float> wmove_apply(const WMove& A, V3<float> x) {
+  const float dx = x.x - A.p[0], dy = x.y - A.p[1], dz = x.z - A.p[2];
+  return v3<float>(fmaf(A.m[0], dx, fmaf(A.m[1], dy, fmaf(A.m[2], dz, A.q[0]))),
+                   fmaf(A.m[3], dx, fmaf(A.m[4], dy, fmaf(A.m[5], dz, A.q[1]))),
+                   fmaf(A.m[6], dx, fmaf(A.m[7], dy, fmaf(A.m[8], dz, A.q[2]))));
+}
+// B o A, about A's point
+__device__ __forceinline__ WMove wmove_compose(const WMove& B, const WMove& A) {
+  WMove r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      r.m[3 * i + j] = B.m[3 * i] * A.m[j] + B.m[3 * i + 1] * A.m[3 + j] + B.m[3 * i + 2] * A.m[6 + j];
+  const V3<float> q = wmove_apply(B, v3<float>(A.q[0], A.q[1], A.q[2]));
+  r.p[0] = A.p[0]; r.p[1] = A.p[1]; r.p[2] = A.p[2];
+  r.q[0] = q.x; r.q[1] = q.y; r.q[2] = q.z;
+  return r;
+}
+// 12 stored values: M and a point (p for a rotation, whose q is p; q for A21,
+// whose p is A1's)
+__device__ __forceinline__ void wstore(float* dst, const WMove& A, const float* pt) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dst[i] = A.m[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dst[9 + i] = pt[i];
+}
+__device__ __forceinline__ void wload_rot(const float* src, WMove& A) {
+  const Pt4<float>* v = reinterpret_cast<const Pt4<float>*>(src);
+  const Pt4<float> a = v[0], b = v[1], d = v[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.p[0] = A.q[0] = d.y; A.p[1] = A.q[1] = d.z; A.p[2] = A.q[2] = d.w;
+}
+__device__ __forceinline__ void wload_21(const float* src, const float* p1, WMove& A) {
+  const Pt4<float>* v = reinterpret_cast<const Pt4<float>*>(src);
+  const Pt4<float> a = v[0], b = v[1], d = v[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.q[0] = d.y; A.q[1] = d.z; A.q[2] = d.w;
+  A.p[0] = p1[0]; A.p[1] = p1[1]; A.p[2] = p1[2];
+}
+
+__device__ __forceinline__ float wdist2(V3<float> a, V3<float> b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ double wsumd(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// G(s) of the warp's chain in FP64 (the warp's parallel scan of residue
+// transforms), stored in FP32; every chunk sphere becomes stale.
+__device__ void wrebuild(WShm& w, const Geom<double>& g, const double* kb, int L, int nJ) {
+  __syncwarp();
+  build_chains_scan(
+      g, kb, L, 1, [&](int, int k) { return (double)w.theta[k]; },
+      [&](int, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
+        w.set_axis(i, 0, v3<float>((float)CA.x, (float)CA.y, (float)CA.z));
+        const V3<double> u1 = unit(CA - N), u2 = unit(Cc - CA);
+        w.set_axis(i, 1, v3<float>((float)u1.x, (float)u1.y, (float)u1.z));
+        w.set_axis(i, 2, v3<float>((float)u2.x, (float)u2.y, (float)u2.z));
+        w.set_x(i, v3<float>((float)CB.x, (float)CB.y, (float)CB.z));
+      },
+      nullptr, nullptr, 32);
+  for (int j = threadIdx.x & 31; j < nJ; j += 32) w.clean[j] = 0;
+  __syncwarp();
+}
+
+// Bounding spheres of the chunks that hold fixed atoms [f0, f1): a chunk
+// whose fixed part lies inside its unmoved range keeps its sphere, the others
+// get one over the whole chunk (box centre, largest distance).
+__device__ void wspheres(WShm& w, int L, int f0, int f1) {
+  const int lane = threadIdx.x & 31;
+  const int j0 = f0 / kWC, j1 = (f1 - 1) / kWC;
+  for (int j = j0 + lane; j <= j1; j += 32) {
+    const int fa = max(kWC * j, f0), fb = min(kWC * j + kWC, f1);
+    const int cl = w.clean[j];
+    if ((cl & 0xffff) <= fa && fb <= (cl >> 16)) continue;
+    const int ca = kWC * j, ce = min(ca + kWC, L);
+    V3<float> lo = w.x(ca), hi = lo;
+    for (int f = ca + 1; f < ce; ++f) {
+      const V3<float> y = w.x(f);
+      lo = v3<float>(fminf(lo.x, y.x), fminf(lo.y, y.y), fminf(lo.z, y.z));
+      hi = v3<float>(fmaxf(hi.x, y.x), fmaxf(hi.y, y.y), fmaxf(hi.z, y.z));
+    }
+    const V3<float> o = (lo + hi) * 0.5f;
+    float r2 = 0.f;
+    for (int f = ca; f < ce; ++f) r2 = fmaxf(r2, wdist2(w.x(f), o));
+    Pt4<float> q;
+    q.x = o.x;
+    q.y = o.y;
+    q.z = o.z;
+    q.w = sqrtf(r2);
+    w.fsph[j] = q;
+    w.clean[j] = ca | (ce << 16);
+  }
+  __syncwarp();
+}
+
+// One item: moving atom m against the fixed atoms of chunk j inside [f0, f1).
+template <bool FUSED, bool TEX>
+__device__ __forceinline__ void witem(const WShm& w, const Tab<float>& tb, long long tab_off, int L,
+                                      int m, int j, int f0, int f1, const WMove& A1,
+                                      const WMove& A2, const WMove& A21, float& acc1, float& acc2,
+                                      float& acc21, unsigned long long& count) {
+  const V3<float> xm = w.x(m);
+  const V3<float> y1 = wmove_apply(A1, xm);
+  V3<float> y2 = xm, y21 = xm;
+  if (FUSED) {
+    y2 = wmove_apply(A2, xm);
+    y21 = wmove_apply(A21, xm);
+  }
+  const int fb = max(kWC * j, f0), fe = min(kWC * j + kWC, f1);
+  // rows of the pairs (f, m): contiguous in f when m < f; when f < m,
+  // r(f+1, m) - r(f, m) = L - f - 2
+  const bool mfirst = m < fb;
+  const int r0 = mfirst ? row_of(L, m, fb) : row_of(L, fb, m);
+  const float2* row = tb.E + tab_off + (long long)r0 * tb.Bp;
+  int rowe = (int)tab_off + r0 * tb.Bp;
+  int step = mfirst ? 1 : L - fb - 2;
+  const int dstep = mfirst ? 0 : -1;
+#pragma unroll 4
+  for (int f = fb; f < fe; ++f) {
+    const V3<float> xf = w.x(f);
+    float e0, e1, e2 = 0.f, e21 = 0.f;
+    if constexpr (TEX) {
+      e0 = pair_term_tex(rowe, dist_fast(xf, xm), tb);
+      e1 = pair_term_tex(rowe, dist_fast(xf, y1), tb);
+      if (FUSED) {
+        e2 = pair_term_tex(rowe, dist_fast(xf, y2), tb);
+        e21 = pair_term_tex(rowe, dist_fast(xf, y21), tb);
+      }
+      rowe += step * tb.Bp;
+    } else {
+      e0 = pair_term(row, dist_fast(xf, xm), tb);
+      e1 = pair_term(row, dist_fast(xf, y1), tb);
+      if (FUSED) {
+        e2 = pair_term(row, dist_fast(xf, y2), tb);
+        e21 = pair_term(row, dist_fast(xf, y21), tb);
+      }
+      row += (long long)step * tb.Bp;
+    }
+    acc1 += e1 - e0;
+    if (FUSED) {
+      acc2 += e2 - e0;
+      acc21 += e21 - e1;
+    }
+    step += dstep;
+  }
+  count += (unsigned long long)(fe - fb) * (FUSED ? 4 : 2);
+}
+
+// Delta-E of move 1, of move 2 and of move 2 after move 1 (FUSED) over the
+// straddle block without its flat far field; every lane returns the sums.
+template <bool FUSED, bool TEX>
+__device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, int m0, int m1,
+                       int f0, int f1, float cut, float& s1, float& s2, float& s21,
+                       unsigned long long& count) {
+  const int lane = threadIdx.x & 31;
+  const int j0 = f0 / kWC, j1 = (f1 - 1) / kWC;
+  WMove A1, A2, A21;
+  wload_rot(w.maps, A1);
+  A2 = A1;
+  A21 = A1;
+  if (FUSED) {
+    wload_rot(w.maps + 12, A2);
+    wload_21(w.maps + 24, A1.p, A21);
+  }
+  float acc1 = 0.f, acc2 = 0.f, acc21 = 0.f;
+  const int nM = m1 - m0;
+  int nq = 0;  // listed items not yet run (the same on every lane)
+  for (int base = 0; base < nM; base += 32) {
+    const int mi = base + lane;
+    ChunkBits b = 0;
+    if (mi < nM) {
+      // the sphere of the moving atom's images, against every chunk
+      const V3<float> xm = w.x(m0 + mi);
+      const V3<float> y1 = wmove_apply(A1, xm);
+      V3<float> o;
+      float r2;
+      if (FUSED) {
+        const V3<float> y2 = wmove_apply(A2, xm), y21 = wmove_apply(A21, xm);
+        o = (xm + y1 + y2 + y21) * 0.25f;
+        r2 = fmaxf(fmaxf(wdist2(xm, o), wdist2(y1, o)), fmaxf(wdist2(y2, o), wdist2(y21, o)));
+      } else {
+        o = (xm + y1) * 0.5f;
+        r2 = fmaxf(wdist2(xm, o), wdist2(y1, o));
+      }
+      const float reach = sqrtf(r2) + cut;
+      for (int j = j0; j <= j1; ++j) {
+        const Pt4<float> q = w.fsph[j];
+        const float lim = reach + q.w;
+        if (wdist2(o, v3<float>(q.x, q.y, q.z)) < lim * lim) b |= ChunkBits(1) << j;
+      }
+    }
+    // list this round's items after the ones waiting
+    const int cnt = __popcll(b);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = nq + incl - cnt;
+    while (b) {
+      const int j = __ffsll((long long)b) - 1;
+      b &= b - 1;
+      w.list[pos++] = (unsigned short)((mi << 6) | j);
+    }
+    nq += total;
+    __syncwarp();
+    if (nq >= 32) {
+      // run whole batches of 32; the rest waits for the next round
+      const int nrun = nq & ~31;
+      for (int q = lane; q < nrun; q += 32) {
+        const int it = w.list[q];
+        witem<FUSED, TEX>(w, tb, tab_off, L, m0 + (it >> 6), it & 63, f0, f1, A1, A2, A21, acc1,
+                          acc2, acc21, count);
+      }
+      const int rem = nq - nrun;
+      const unsigned short v = lane < rem ? w.list[nrun + lane] : (unsigned short)0;
+      __syncwarp();
+      if (lane < rem) w.list[lane] = v;
+      __syncwarp();
+      nq = rem;
+    }
+  }
+  if (lane < nq) {
+    const int it = w.list[lane];
+    witem<FUSED, TEX>(w, tb, tab_off, L, m0 + (it >> 6), it & 63, f0, f1, A1, A2, A21, acc1, acc2,
+                      acc21, count);
+  }
+  s1 = wsum(acc1);
+  s2 = wsum(acc2);
+  s21 = wsum(acc21);
+}
+
+// V of the warp's chain from its current coordinates: FP32 terms, FP64 sums
+// (Eq. 5 over a < b); every lane returns it.
+__device__ double wenergy(const WShm& w, const Tab<float>& tb, long long tab_off, int L) {
+  const int lane = threadIdx.x & 31;
+  const int nch = (L - 1 + kWC - 1) / kWC;
+  const int items = L * nch;
+  double acc = 0.0;
+  for (int it = lane; it < items; it += 32) {
+    const int a = it / nch, ch = it - a * nch;
+    const int b0 = a + 1 + ch * kWC;
+    const int b1 = min(L, b0 + kWC);
+    if (b0 >= b1) continue;
+    const V3<float> xa = w.x(a);
+    const float2* row = tb.E + tab_off + (long long)row_of(L, a, b0) * tb.Bp;
+    float part = 0.f;
+    for (int b = b0; b < b1; ++b, row += tb.Bp) part += pair_term(row, dist_(xa, w.x(b)), tb);
+    acc += (double)part;
+  }
+  return wsumd(acc);
+}
+
+template <bool TEX>
+__device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb, const GroupDev& G,
+                           const ProteinDev& P, int nJ) {
+  const int lane = threadIdx.x & 31;
+  const int L = P.L, n = P.n;
+  const int chain = G.chain0;
+  const long long toff = P.tors0 + (long long)(chain - P.chain0) * n;
+  for (int k = lane; k < n; k += 32) w.theta[k] = a.theta[toff + k];
+  const long long t0 = a.tcount[chain];
+  const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
+  const double Tc = a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
+  const bool traced = chain < a.trace_chains;
+  // decisions need Delta-E only and the exit recomputes V from scratch, so
+  // the entry and periodic resyncs rebuild the coordinates alone
+  wrebuild(w, a.geom64, kb, L, nJ);
+  long long since = 0, nacc = 0;
+  unsigned long long count = 0;
+  long long d0 = 0, dend = 0;
+  int kn = (int)(t0 % n);
+  for (long long j = 0; j < steps;) {
+    if (j + 2 > dend) {
+      __syncwarp();
+      d0 = j;
+      dend = j + kWDraw;
+      for (int q = lane; q < kWDraw; q += 32) {
+        float z, lnu;
+        normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)(t0 + j + q), 0u),
+                       &z, &lnu);
+        w.draws[2 * q] = z;
+        w.draws[2 * q + 1] = lnu;
+      }
+      __syncwarp();
+    }
+    const long long t = t0 + j;
+    const int k = kn;
+    if (since >= a.resync_every || (k == 0 && j > 0)) {
+      wrebuild(w, a.geom64, kb, L, nJ);
+      since = 0;
+    }
+    const bool fused = (k & 1) && (k + 1 < n) && (j + 1 < steps);
+    const int p = (k + 1) >> 1;
+    const bool up = p <= L - p;  // move the upstream side (it is the smaller)
+    const int m0 = up ? 0 : p, m1 = up ? p : L;
+    const int f0 = up ? p : 0, f1 = up ? L : p;
+    const bool dead = (k == 0) || (k == n - 1);
+    // three lanes form the maps: lane 0 move 1's A1, lane 1 move 2's A2
+    // about its own axis, lane 2 A1 again and then move 2 about its axis as
+    // move 1 left it, composed after A1 (the CTA kernel's arithmetic)
+    if (lane == 0 || (lane < 3 && fused)) {
+      const int k1 = lane == 1 ? k + 1 : k;
+      const float z = w.draws[2 * (j + (k1 - k) - d0)];
+      const float lnu = w.draws[2 * (j + (k1 - k) - d0) + 1];
+      const float th = w.theta[k1];
+      const float thn = propose(th, z, a.sigma, a.lattice_K);
+      if (lane < 2) {
+        w.maps[36 + lane] = thn;
+        w.maps[38 + lane] = lnu;
+      }
+      if (!dead) {
+        // k1 odd: psi_i about CA_i -> C_i; k1 even: phi_i about N_i -> CA_i
+        const int i = k1 >> 1;
+        const float d = wrap_angle(thn - th);
+        const WMove A = wmove_rotation(w.axis(i, 0), w.axis(i, (k1 & 1) ? 2 : 1), up ? -d : d);
+        if (lane < 2) {
+          wstore(w.maps + 12 * lane, A, A.p);
+        } else {
+          const float z2 = w.draws[2 * (j + 1 - d0)];
+          const float th2 = w.theta[k + 1];
+          const float d2 = wrap_angle(propose(th2, z2, a.sigma, a.lattice_K) - th2);
+          const V3<float> P2 = w.axis(p, 0), u2 = w.axis(p, 1);  // phi_p: N_p -> CA_p
+          const V3<float> P2m = up ? P2 : wmove_apply(A, P2);
+          const V3<float> u2m = up ? u2 : wmove_lin(A, u2);
+          const WMove A21 = wmove_compose(wmove_rotation(P2m, u2m, up ? -d2 : d2), A);
+          wstore(w.maps + 24, A21, A21.q);
+        }
+      }
+    }
+    __syncwarp();
+    if (dead) {
+      // phi_0 and psi_{L-1} move no C-beta: Delta-E = 0, always accepted
+      const float thn = w.maps[36], lnu = w.maps[38];
+      const int acc = (double)lnu * Tc < -0.0;
+      if (lane == 0) {
+        if (acc) w.theta[k] = thn;
+        if (traced && t < a.trace_cap) {
+          TraceRec r;
+          r.k = k;
+          r.accept = acc;
+          r.theta_new = (double)thn;
+          r.lnu = (double)lnu;
+          r.dE = 0.0;
+          a.trace[(size_t)chain * a.trace_cap + t] = r;
+        }
+      }
+      nacc += acc;
+      __syncwarp();
+      j += 1;
+      since += 1;
+      kn = k + 1 < n ? k + 1 : 0;
+      continue;
+    }
+    wspheres(w, L, f0, f1);
+    float s1, s2, s21;
+    if (fused)
+      wblock<true, TEX>(w, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21, count);
+    else
+      wblock<false, TEX>(w, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21, count);
+    // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE, taken by every lane
+    const double d1 = s1, d2 = s2, d21 = s21;
+    const float thn1 = w.maps[36], lnu1 = w.maps[38];
+    const int acc1 = (double)lnu1 * Tc < -d1;
+    int code = acc1, acc2 = 0;
+    double e2 = 0.0;
+    if (fused) {
+      e2 = acc1 ? d21 : d2;
+      acc2 = (double)w.maps[39] * Tc < -e2;
+      if (acc2) code = acc1 ? 3 : 2;
+    }
+    if (lane == 0) {
+      if (acc1) w.theta[k] = thn1;
+      if (traced && t < a.trace_cap) {
+        TraceRec r;
+        r.k = k;
+        r.accept = acc1;
+        r.theta_new = (double)thn1;
+        r.lnu = (double)lnu1;
+        r.dE = d1;
+        a.trace[(size_t)chain * a.trace_cap + t] = r;
+      }
+      if (fused) {
+        if (acc2) w.theta[k + 1] = w.maps[37];
+        if (traced && t + 1 < a.trace_cap) {
+          TraceRec r;
+          r.k = k + 1;
+          r.accept = acc2;
+          r.theta_new = (double)w.maps[37];
+          r.lnu = (double)w.maps[39];
+          r.dE = e2;
+          a.trace[(size_t)chain * a.trace_cap + t + 1] = r;
+        }
+      }
+    }
+    nacc += acc1 + acc2;
+    if (code) {
+      // commit: the moving side turns by the accepted map; an upstream move
+      // turns only C-betas (the rest of this sweep rotates about bonds at or
+      // after the pivot, and a new sweep starts from a rebuild)
+      WMove A;
+      if (code < 3)
+        wload_rot(w.maps + 12 * (code - 1), A);
+      else
+        wload_21(w.maps + 24, w.maps + 9, A);
+      const int per = up ? 1 : 4;
+      const int total = (m1 - m0) * per;
+      for (int idx = lane; idx < total; idx += 32) {
+        const int v = up ? 3 : (idx & 3), i = m0 + (up ? idx : idx >> 2);
+        if (v == 0)
+          w.set_axis(i, 0, wmove_apply(A, w.axis(i, 0)));
+        else if (v < 3)
+          w.set_axis(i, v, wmove_lin(A, w.axis(i, v)));
+        else
+          w.set_x(i, wmove_apply(A, w.x(i)));
+      }
+      // the chunks' unmoved ranges lose [m0, m1)
+      if (up) {
+        for (int jj = lane; jj <= (p - 1) / kWC; jj += 32) {
+          const int cl = w.clean[jj];
+          w.clean[jj] = max(cl & 0xffff, p) | (cl & ~0xffff);
+        }
+      } else {
+        for (int jj = p / kWC + lane; jj < nJ; jj += 32) {
+          const int cl = w.clean[jj];
+          w.clean[jj] = (cl & 0xffff) | (min(cl >> 16, p) << 16);
+        }
+      }
+    }
+    __syncwarp();
+    j += fused ? 2 : 1;
+    kn = k + (fused ? 2 : 1);
+    if (kn >= n) kn -= n;
+    since += fused ? 2 : 1;
+  }
+  // exit: V from scratch (FP64 sum) of the current coordinates (their drift
+  // since the last rebuild is ~1e-5 A)
+  __syncwarp();
+  const double e = wenergy(w, a.tab, P.tab_off, L);
+  int better = 0;
+  if (lane == 0) {
+    if (!(e == e)) atomicOr(a.err, 1);  // NaN energy
+    a.E_cur[chain] = e;
+    a.tcount[chain] = t0 + steps;
+    if (a.acc_out) a.acc_out[chain] = nacc;
+    if (a.trace_count && traced)
+      a.trace_count[chain] = t0 + steps < a.trace_cap ? t0 + steps : a.trace_cap;
+    if (e < a.best_E[chain]) {
+      a.best_E[chain] = e;
+      better = 1;
+    }
+  }
+  better = __shfl_sync(0xffffffffu, better, 0);
+  for (int k = lane; k < n; k += 32) {
+    const float v = w.theta[k];
+    a.theta[toff + k] = v;
+    if (better) a.best_theta[toff + k] = v;
+  }
+  if (a.coords) {
+    const long long off = 3 * (toff / 2);
+    for (int i = lane; i < L; i += 32) {
+      const V3<float> x = w.x(i);
+      a.coords[off + 3 * i] = x.x;
+      a.coords[off + 3 * i + 1] = x.y;
+      a.coords[off + 3 * i + 2] = x.z;
+    }
+  }
+  unsigned long long c = count;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if (lane == 0 && a.pair_count && c) atomicAdd(a.pair_count, c);
+  __syncwarp();
+}
+
+template <bool TEX>
+__global__ void __launch_bounds__(256) gwarp_kernel(SweepArgs<float> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  double* kb = reinterpret_cast<double*>(smem);
+  residue_basis(a.geom64, kb);  // the whole CTA, once
+  const WLayout lay(a.Lmax);
+  WShm w(smem + kKbBytes + (size_t)(threadIdx.x >> 5) * lay.total, lay);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(a.queue, 1);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= a.ngroups) break;
+    const GroupDev G = a.groups[g];
+    wrun_chain<TEX>(w, a, kb, G, a.prot[G.protein], lay.nJ);
+  }
+}
+
+}  // namespace
+
+size_t gwarp_smem_bytes(int Lmax, int warps) {
+  return kKbBytes + (size_t)warps * WLayout(Lmax).total;
+}
+
+cudaError_t gwarp_set_smem(size_t optin) {
+  cudaError_t e = allow_dynamic_smem(gwarp_kernel<true>, optin);
+  if (e != cudaSuccess) return e;
+  return allow_dynamic_smem(gwarp_kernel<false>, optin);
+}
+
+cudaError_t gwarp_occupancy(int warps, size_t smem, int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, gwarp_kernel<true>, 32 * warps,
+                                                       smem);
+}
+
+cudaError_t launch_gwarp(const SweepArgs<float>& a, int warps, int grid, cudaStream_t st) {
+  const size_t sm = gwarp_smem_bytes(a.Lmax, warps);
+  if (a.tab.tex)
+    gwarp_kernel<true><<<grid, 32 * warps, sm, st>>>(a);
+  else
+    gwarp_kernel<false><<<grid, 32 * warps, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace amh

@@ -101,6 +101,13 @@ cudaError_t global_set_smem(size_t bytes);
 template <class R, int C, bool ST>
 cudaError_t global_occupancy(int threads, size_t smem, int* per_sm);
 
+// Global sweeps with one warp per chain (FP32, far field skipped, no staging):
+// `warps` chains per CTA; groups of one chain each.
+size_t gwarp_smem_bytes(int Lmax, int warps);
+cudaError_t gwarp_set_smem(size_t optin);
+cudaError_t gwarp_occupancy(int warps, size_t smem, int* per_sm);
+cudaError_t launch_gwarp(const SweepArgs<float>& a, int warps, int grid, cudaStream_t st);
+
 // Window C-betas of proposal k (window d) built by the local sweep kernel's
 // window builder from one chain's torsions (device pointer theta, n values),
 // in the frame of the window's first residue: out[(r - lo) * 3 + xyz].

@@ -80,9 +80,9 @@ def test_fresh_build_equals_oracle(amh, orc, precision, L):
     print("fresh build L=%d FP%d: max deviation %.3g A" % (L, precision, worst))
 
 
-@pytest.mark.parametrize("precision,C", [(32, 0), (32, 4), (64, 1)])
+@pytest.mark.parametrize("precision,C,kernel", [(32, 2, 2), (32, 4, 1), (64, 1, 1)])
 @pytest.mark.parametrize("L", [150, 300])
-def test_coordinates_after_moves_equal_oracle(amh, orc, precision, C, L):
+def test_coordinates_after_moves_equal_oracle(amh, orc, precision, C, kernel, L):
     """A global sweep of n - 1 proposals (it ends before the next sweep's
     rebuild) with no periodic resync: every accepted move since the entry
     rebuild has turned the coordinates; at the end they must still be G(s) of
@@ -93,16 +93,29 @@ def test_coordinates_after_moves_equal_oracle(amh, orc, precision, C, L):
     prot = synth.make_protein(L, seed=910 + L)
     tors = synth.random_torsions(chains, L, seed=911)
     tol = 1e-3 if precision == 32 else 1e-10
+    P = orc.Problem(L, prot.p, prot.edges)
+    s_orc = tors.astype(np.float64)
+    t0 = 0
     with amh.Sampler(prot, chains, tors, precision=precision, keep_coords=1,
-                     resync_every=1 << 30, chains_per_cta=C) as s:
+                     resync_every=1 << 30, chains_per_cta=C, global_kernel=kernel) as s:
+        assert s.launch_config()[3] == kernel
         for steps in (n - 1, n // 2 + 1):
             acc = s.sweep(1, 0, 0.8, 10 * DEG, steps, 17)
             assert acc.min() > steps // 20  # many moves were committed
             X = s.coords()
             th = s.torsions()
+            if precision == 64:
+                # the FP64 form's torsions are read back through the FP32
+                # interface; its own FP64 state is the oracle's trajectory
+                # (the FP64 form takes the oracle's decisions)
+                s_orc = np.stack([P.run(s_orc[c], orc.GLOBAL, 0, 0.8, 10 * DEG, t0, steps, 17,
+                                        c)[0] for c in range(chains)])
+                assert np.all(np.abs(np.angle(np.exp(1j * (th - s_orc)))) <= 1e-6)
+            t0 += steps
             worst = (0.0, 0.0)
             for c in range(chains):
-                want = orc.build_coords(th[c].astype(np.float64))["CB"]
+                want = orc.build_coords(th[c].astype(np.float64) if precision == 32
+                                        else s_orc[c])["CB"]
                 dd = max_dist_dev(X[c], want)
                 sd = superposed_max_dev(X[c], want)
                 worst = (max(worst[0], dd), max(worst[1], sd))
