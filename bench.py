@@ -49,7 +49,7 @@ TRAFFIC_CAPTURE = {"sources_sha1": "f8ad6549657570d42f338336b41903fef0a11d73",
                                "paper_2211_03193_gb300/csrc/amh_device.cuh",
                                "paper_2211_03193_gb300/csrc/amh_internal.h"],
                    "workload": "amh_L300_c1024",
-                   "bytes": {(1, 128, 0): 16218368}}
+                   "bytes": {(1, 1, 128, 0): 16218368}}
 
 
 def captured_traffic(workload_name, shape):
@@ -272,21 +272,25 @@ def measured_peaks():
                    "2048 threads per SM; 16-byte L1-bypassing loads over half the L2"}
 
 
-def time_to_target(stream_cls=None):
-    """Time to a low-energy structure, after the protocol of Sec. 3 / Fig. 4E:
-    the CPU (the FP64 oracle, one chain per core, 10 seeds) runs 1e5
-    proposals of the AMH schedule on the L=150 protein; the target E* is the
-    mean over the 10 runs of the lowest energy seen (at global-sweep ends);
-    the GPU then runs 1024 chains of the same schedule until the lowest
-    energy over its chains reaches E*.  Returns both wall times."""
+def time_to_target():
+    """Time to a low-energy structure, after the protocol of Sec. 3 / Fig. 4E,
+    over the whole anneal: the CPU (the FP64 oracle, one chain per core, 10
+    seeds) runs the full L=150 schedule (2e5 proposals per chain, 10 local :
+    1 global, T 2.0 -> 0.05, sigma 10 -> 4 deg); the target E* is the mean
+    over the 10 runs of the lowest energy each reached (at global-sweep
+    ends).  The GPU then runs 1024 chains of the same schedule until the
+    lowest energy over its chains reaches E*.  The target lies at the end of
+    the anneal, so the GPU has to anneal towards it (a target taken from a
+    short CPU run is met by the spread of 1024 chains at high temperature).
+    Returns both wall times and the sweep at which the GPU got there."""
     import torch
     import oracle
     from paper_2211_03193_gb300 import _amh, synth
     from paper_2211_03193_gb300.sampler import Sampler
     w = workload("amh_L150_c1024")
     L, n = w["L"], w["n"]
-    total = 100000 // n
-    sched = schedule_for(dict(w, total_sweeps=total), seed=2)
+    total = w["total_sweeps"]
+    sched = schedule_for(w, seed=2)
     prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
                               seed=w["seed"])
     P = oracle.Problem(L, prot.p, prot.edges)
@@ -319,13 +323,18 @@ def time_to_target(stream_cls=None):
                     reached = True
                     break
     gpu_s = time.perf_counter() - t0
+    final_best = float(bE.min())
     samp.close()
-    return {"protein": "L=150, 37 bins (amh_L150_c1024 schedule over 1e5 proposals)",
+    return {"protein": "L=150, 37 bins (amh_L150_c1024 schedule, %d sweeps = 2e5 proposals "
+                       "per chain)" % total,
             "target_energy": target, "cpu_runs": runs, "cpu_seconds": cpu_s,
-            "cpu_proposals_per_run": total * n, "gpu_chains": chains, "gpu_seconds": gpu_s,
-            "gpu_sweeps": s + 1, "reached": reached,
-            "speedup": cpu_s / gpu_s if reached else None,
-            "note": "CPU: FP64 oracle, one chain per core, wall time of the 10 parallel runs"}
+            "cpu_proposals_per_run": total * n, "cpu_best_per_run": [float(v) for v in best],
+            "gpu_chains": chains, "gpu_seconds": gpu_s, "gpu_sweeps": s + 1,
+            "gpu_sweeps_total": total, "gpu_best_when_stopped": final_best,
+            "reached": reached, "speedup": cpu_s / gpu_s if reached else None,
+            "note": "CPU: FP64 oracle, one chain per core, wall time of the 10 parallel runs; "
+                    "GPU: wall time from the first sweep until the best of its chains reaches "
+                    "the CPU runs' mean lowest energy, checked after every global sweep"}
 
 
 def run_schemes():
@@ -370,19 +379,22 @@ def run_schemes():
                           "median_final_energy": float(np.median(E))}))
 
 
-def run_forms():
+def run_forms(name=WORKLOAD):
     """The batched FP32 form against the plain FP64 form (one chain per
-    launch) on the same GPU, L=300: proposals/s of one AMH cycle."""
+    launch) and the batched FP64 form on the same GPU: proposals/s of one AMH
+    cycle of the workload's schedule, and the FP32 form's end energies
+    against the FP64 form's energies of the same states."""
     import torch
     from paper_2211_03193_gb300 import _amh, synth
     from paper_2211_03193_gb300.sampler import Sampler
-    w = workload("amh_L300_c1024")
-    L, n = w["L"], w["n"]
+    w = workload(name)
+    L, n, nch = w["L"], w["n"], w["chains"]
     prot = synth.make_protein(L, edges=synth.edges_by_name(w["bins"]), sigma_d=w["sigma_d"],
                               seed=w["seed"])
     sched = schedule_for(w, seed=1)
-    for label, chains, prec in (("fp32_batched_1024", 1024, 32), ("fp32_one_chain", 1, 32),
-                                ("fp64_one_chain", 1, 64)):
+    ends = {}
+    for label, chains, prec in (("fp32_batched_%d" % nch, nch, 32), ("fp32_one_chain", 1, 32),
+                                ("fp64_one_chain", 1, 64), ("fp64_batched_%d" % nch, nch, 64)):
         tors = synth.random_torsions(chains, L, seed=w["start_seed"])
         stream = torch.cuda.Stream()
         with Sampler(prot, chains, tors, precision=prec, stream=stream) as s:
@@ -400,46 +412,79 @@ def run_forms():
                 e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-        print(json.dumps({"experiment": "forms", "form": label, "L": L, "chains": chains,
-                          "precision": prec, "ms_per_cycle": ms,
+            if chains == nch:
+                ends[prec] = s.state()[:2]
+        print(json.dumps({"experiment": "forms", "workload": name, "form": label, "L": L,
+                          "chains": chains, "precision": prec, "ms_per_cycle": ms,
                           "proposals_per_s": w["cycle"] * n * chains / (ms / 1000.0)}))
+    # the FP32 form's energies against the FP64 form's energies of the same states
+    th32, E32 = ends[32]
+    with Sampler(prot, nch, th32, precision=64) as s64:
+        E64 = s64.energy()
+    rel = np.abs(E32 - E64) / np.abs(E64)
+    print(json.dumps({"experiment": "forms", "workload": name,
+                      "fp32_vs_fp64_energy_rel_max": float(rel.max()),
+                      "fp32_vs_fp64_energy_rel_median": float(np.median(rel))}))
 
 
 def run_batched():
     """64 proteins with L uniform in [50, 400], 256 chains each, one context:
     one AMH cycle (10 local + 1 global sweep per chain) through the persistent
-    work queue; proposals/s over all chains."""
+    work queue, issued eagerly (one library call per sweep) and replayed from
+    a CUDA graph captured from the same calls; proposals/s over all chains."""
     import torch
     from paper_2211_03193_gb300 import _amh, synth
-    from paper_2211_03193_gb300.sampler import Sampler
+    from paper_2211_03193_gb300.sampler import Sampler, Schedule, capture_schedule
     w = dict(synth.WORKLOADS["amh_batched_64prot"])
     Ls = synth.uneven_lengths(w["nproteins"], w["Lmin"], w["Lmax"], seed=3)
     prots = [synth.make_protein(L, seed=w["seed"] + i) for i, L in enumerate(Ls)]
     chains = [w["chains"]] * len(Ls)
     tors = np.concatenate([synth.random_torsions(w["chains"], L, seed=w["start_seed"] + i).ravel()
                            for i, L in enumerate(Ls)])
+    # one cycle at fixed T and sigma, repeated (the schedule's cycle length)
+    sched = Schedule(total_sweeps=11, n_local=10, n_global=1, window=w["window"], T0=1.0, T1=1.0,
+                     sigma0_deg=10.0, sigma1_deg=10.0, seed=1)
+    props = sum(11 * 2 * L * w["chains"] for L in Ls)
+    out = {"experiment": "batched", "proteins": len(Ls), "chains": sum(chains),
+           "L_range": [min(Ls), max(Ls)], "proposals_per_cycle": props}
+    reps = 5
     stream = torch.cuda.Stream()
     with Sampler(prots, chains, tors, resync_every=w["resync_every"], stream=stream) as s:
         def cycle():
             for q in range(11):
-                mode = 0 if q < 10 else 1
-                _amh.amh_sweeps(s.ctx, mode, w["window"], 1.0, math.radians(10.0), 1, 1, None)
+                mode, T, sigma = sched.params(q)
+                _amh.amh_sweeps(s.ctx, mode, w["window"], T, sigma, 1, 1, None)
         with torch.cuda.stream(stream):
             cycle()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             e0.record(stream)
-            cycle()
+            for _ in range(reps):
+                cycle()
             e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = e0.elapsed_time(e1) / reps
         C, thr, D, K = s.launch_config()
-    props = sum(11 * 2 * L * w["chains"] for L in Ls)
-    print(json.dumps({"experiment": "batched", "proteins": len(Ls), "chains": sum(chains),
-                      "L_range": [min(Ls), max(Ls)], "ms_per_cycle": ms,
-                      "proposals_per_s": props / (ms / 1000.0), "chains_per_cta": C,
-                      "threads_per_cta": thr}))
+        out.update({"eager_ms_per_cycle": ms, "eager_proposals_per_s": props / (ms / 1000.0),
+                    "chains_per_cta": C, "threads_per_cta": thr, "global_kernel": K})
+    gstream = torch.cuda.Stream()
+    with Sampler(prots, chains, tors, resync_every=w["resync_every"], stream=gstream) as s:
+        g = capture_schedule(s, sched, 0, 11, gstream)
+        g.replay()  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(gstream):
+            e0.record(gstream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(gstream)
+        torch.cuda.synchronize()
+        ms_g = e0.elapsed_time(e1) / reps
+        assert s.counter(0) == (reps + 1) * 11 * 2 * Ls[0]
+        out.update({"graph_ms_per_cycle": ms_g, "graph_proposals_per_s": props / (ms_g / 1000.0),
+                    "launches_per_cycle": 11})
+    print(json.dumps(out))
 
 
 def run_grad():
@@ -732,13 +777,19 @@ def run_ours(args):
     achieved = evals_glob_launch * FLOP_PER_EVAL / (g_ms / 1000.0) / 1e12
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fetch = (", table rows staged %d deep" % D if D else
+             (", table entries through the texture path" if args.texture != 2
+              else ", table entries through L1 loads"))
+    if K == 2:
+        kname = "gwarp_kernel<%s> (global sweep, one warp per chain, %d chains per CTA%s)" % (
+            "true" if args.texture != 2 else "false", C, fetch)
+    else:
+        kname = "global_kernel<float,%d,%s> (global sweep, %d threads/CTA%s)" % (
+            C, "true" if D else "false", thr, fetch)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-            "frac": achieved / peak_tf, "traffic": captured_traffic(args.workload, (C, thr, D)),
-            "kernel": "global_kernel<float,%d,%s> (global sweep, %d threads/CTA%s)" % (
-                C, "true" if D else "false", thr,
-                ", table rows staged %d deep" % D if D else
-                (", table entries through the texture path" if args.texture != 2
-                 else ", table entries through L1 loads")),
+            "frac": achieved / peak_tf,
+            "traffic": captured_traffic(args.workload, (K, C, thr, D)),
+            "kernel": kname,
             "launch_ms": g_ms, "pair_evals_per_launch": evals_glob_launch,
             "straddle_terms_dense": dense, "straddle_terms_evaluated": int(terms_glob),
             # the rate the same launch time would mean if every straddle pair
@@ -763,9 +814,11 @@ def run_ours(args):
            "config": {"workload": args.workload, "L": L, "chains_per_gpu": chains, "bins": w["bins"], "schedule": "10 local (d=8) : 1 global per step, "
                       "T 2.0->0.05, sigma 10->4 deg over %d sweeps" % w["total_sweeps"],
                       "proposals_per_step_per_gpu": props_step, "l2": "flushed between steps "
-                      "(256 MB write); the %.1f MB table is L2-resident within a step" % (
-                          tab_mb,),
+                      "(256 MB write); the %.1f MB table is read from L2 within a step "
+                      "(L2: 129 MB)" % (tab_mb,),
                       "chains_per_cta": C, "threads_per_cta": thr, "stage_depth": D,
+                      "global_kernel": "one warp per chain" if K == 2 else "chains of a CTA "
+                                       "in lock-step",
                       "gradient": "dV/ds of all %d states once per step (one amh_grad launch); %s" % (
                           chains, "on a second stream beside the global sweep, over the states "
                           "that ended the previous step" if args.overlap else
@@ -793,8 +846,10 @@ def run_ours(args):
 def main():
     args = parse()
     if args.experiment:
-        {"schemes": run_schemes, "forms": run_forms, "batched": run_batched,
-         "grad": run_grad}[args.experiment]()
+        if args.experiment == "forms":
+            run_forms(args.workload)
+            return
+        {"schemes": run_schemes, "batched": run_batched, "grad": run_grad}[args.experiment]()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -38,43 +38,54 @@ constexpr size_t kKbBytes = 1792;  // residue-transform basis: 216 doubles, 128-
 __host__ __device__ inline size_t wal(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Shared memory of one warp (one chain of up to Lmax residues).
+constexpr int kBatch = 32;  // pairs evaluated at a time: one per lane
+constexpr int kPairCap = 32 * kWC + kBatch;  // one round of 32 items of kWC pairs plus a partial batch
+
 struct WLayout {
-  size_t cb, fsph, maps, theta, bb, draws, clean, list, total;
-  int nJ, cap;
+  size_t cb, fsph, msph, isph, maps, theta, bb, draws, clean, plist, kp, total;
+  int nJ;
   __host__ __device__ explicit WLayout(int Lmax) {
     nJ = (Lmax + kWC - 1) / kWC;
-    cap = 32 * nJ + 32;  // items of one round of 32 moving atoms plus a partial batch
     size_t o = 0;
     cb = o;    o = wal(o + sizeof(Pt4<float>) * (size_t)Lmax);
     fsph = o;  o = wal(o + sizeof(Pt4<float>) * (size_t)nJ);
+    msph = o;  o = wal(o + sizeof(Pt4<float>) * (size_t)nJ);
+    isph = o;  o = wal(o + sizeof(Pt4<float>) * (size_t)(Lmax / 2 + 1));
     maps = o;  o = wal(o + sizeof(float) * 40);
     theta = o; o = wal(o + sizeof(float) * 2 * (size_t)Lmax);
     bb = o;    o = wal(o + sizeof(float) * 9 * (size_t)Lmax);
     draws = o; o = wal(o + sizeof(float) * 2 * kWDraw);
     clean = o; o = wal(o + sizeof(int) * (size_t)nJ);
-    list = o;  o = wal(o + sizeof(unsigned short) * (size_t)cap);
+    plist = o; o = wal(o + sizeof(unsigned) * (size_t)kPairCap);
+    kp = o;    o = wal(o + sizeof(unsigned short) * 32);
     total = (o + 127) & ~size_t(127);
   }
 };
 
 struct WShm {
   Pt4<float>* cb;        // [L] C-betas (x, y, z, 0)
-  Pt4<float>* fsph;      // [chunk] bounding sphere (centre, radius)
+  Pt4<float>* fsph;      // [chunk] bounding sphere of the chunk's C-betas (centre, radius)
+  Pt4<float>* msph;      // [moving chunk] sphere holding its atoms' image spheres
+  Pt4<float>* isph;      // [moving atom] sphere of the atom's images under the moves
   float* maps;           // A1 [0,12), A2 [12,24), A21 [24,36); thn [36,38), ln u [38,40)
   float* theta;          // [n]
   float* bb;             // [i][v][xyz]: v 0 CA_i, 1 unit N_i -> CA_i, 2 unit CA_i -> C_i
   float* draws;          // [kWDraw][2]: (z, ln u)
   int* clean;            // [chunk] lo | hi << 16: atoms unmoved since the sphere was made
-  unsigned short* list;  // items (moving atom << 6 | chunk)
+  unsigned* plist;       // pairs within reach, (moving atom << 16 | fixed atom)
+  unsigned short* kp;    // chunk pairs within reach, of one round
   __device__ WShm(unsigned char* base, const WLayout& l) {
     cb = (Pt4<float>*)(base + l.cb);
     fsph = (Pt4<float>*)(base + l.fsph);
+    msph = (Pt4<float>*)(base + l.msph);
+    isph = (Pt4<float>*)(base + l.isph);
     maps = (float*)(base + l.maps);
     theta = (float*)(base + l.theta);
     bb = (float*)(base + l.bb);
     draws = (float*)(base + l.draws);
     clean = (int*)(base + l.clean);
-    list = (unsigned short*)(base + l.list);
+    plist = (unsigned*)(base + l.plist);
+    kp = (unsigned short*)(base + l.kp);
   }
   __device__ V3<float> x(int i) const {
     const Pt4<float> p = cb[i];
@@ -230,67 +241,58 @@ __device__ void wspheres(WShm& w, int L, int f0, int f1) {
   __syncwarp();
 }
 
-// One item: moving atom m against the fixed atoms of chunk j inside [f0, f1).
+// One straddle pair (moving atom m, fixed atom f): its terms at the current
+// coordinates and under the moves, added to the Delta-E sums.
 template <bool FUSED, bool TEX>
-__device__ __forceinline__ void witem(const WShm& w, const Tab<float>& tb, long long tab_off, int L,
-                                      int m, int j, int f0, int f1, const WMove& A1,
-                                      const WMove& A2, const WMove& A21, float& acc1, float& acc2,
-                                      float& acc21, unsigned long long& count) {
-  const V3<float> xm = w.x(m);
+__device__ __forceinline__ void wpair(const WShm& w, const Tab<float>& tb, long long tab_off, int L,
+                                      int m, int f, const WMove& A1, const WMove& A2,
+                                      const WMove& A21, float& acc1, float& acc2, float& acc21) {
+  const V3<float> xm = w.x(m), xf = w.x(f);
+  const int r = m < f ? row_of(L, m, f) : row_of(L, f, m);
   const V3<float> y1 = wmove_apply(A1, xm);
-  V3<float> y2 = xm, y21 = xm;
-  if (FUSED) {
-    y2 = wmove_apply(A2, xm);
-    y21 = wmove_apply(A21, xm);
-  }
-  const int fb = max(kWC * j, f0), fe = min(kWC * j + kWC, f1);
-  // rows of the pairs (f, m): contiguous in f when m < f; when f < m,
-  // r(f+1, m) - r(f, m) = L - f - 2
-  const bool mfirst = m < fb;
-  const int r0 = mfirst ? row_of(L, m, fb) : row_of(L, fb, m);
-  const float2* row = tb.E + tab_off + (long long)r0 * tb.Bp;
-  int rowe = (int)tab_off + r0 * tb.Bp;
-  int step = mfirst ? 1 : L - fb - 2;
-  const int dstep = mfirst ? 0 : -1;
-#pragma unroll 4
-  for (int f = fb; f < fe; ++f) {
-    const V3<float> xf = w.x(f);
-    float e0, e1, e2 = 0.f, e21 = 0.f;
-    if constexpr (TEX) {
-      e0 = pair_term_tex(rowe, dist_fast(xf, xm), tb);
-      e1 = pair_term_tex(rowe, dist_fast(xf, y1), tb);
-      if (FUSED) {
-        e2 = pair_term_tex(rowe, dist_fast(xf, y2), tb);
-        e21 = pair_term_tex(rowe, dist_fast(xf, y21), tb);
-      }
-      rowe += step * tb.Bp;
-    } else {
-      e0 = pair_term(row, dist_fast(xf, xm), tb);
-      e1 = pair_term(row, dist_fast(xf, y1), tb);
-      if (FUSED) {
-        e2 = pair_term(row, dist_fast(xf, y2), tb);
-        e21 = pair_term(row, dist_fast(xf, y21), tb);
-      }
-      row += (long long)step * tb.Bp;
-    }
-    acc1 += e1 - e0;
+  float e0, e1, e2 = 0.f, e21 = 0.f;
+  if constexpr (TEX) {
+    const int rowe = (int)tab_off + r * tb.Bp;
+    e0 = pair_term_tex(rowe, dist_fast(xf, xm), tb);
+    e1 = pair_term_tex(rowe, dist_fast(xf, y1), tb);
     if (FUSED) {
-      acc2 += e2 - e0;
-      acc21 += e21 - e1;
+      e2 = pair_term_tex(rowe, dist_fast(xf, wmove_apply(A2, xm)), tb);
+      e21 = pair_term_tex(rowe, dist_fast(xf, wmove_apply(A21, xm)), tb);
     }
-    step += dstep;
+  } else {
+    const float2* row = tb.E + tab_off + (long long)r * tb.Bp;
+    e0 = pair_term(row, dist_fast(xf, xm), tb);
+    e1 = pair_term(row, dist_fast(xf, y1), tb);
+    if (FUSED) {
+      e2 = pair_term(row, dist_fast(xf, wmove_apply(A2, xm)), tb);
+      e21 = pair_term(row, dist_fast(xf, wmove_apply(A21, xm)), tb);
+    }
   }
-  count += (unsigned long long)(fe - fb) * (FUSED ? 4 : 2);
+  acc1 += e1 - e0;
+  if (FUSED) {
+    acc2 += e2 - e0;
+    acc21 += e21 - e1;
+  }
 }
+
+__device__ __forceinline__ V3<float> wc(Pt4<float> p) { return v3<float>(p.x, p.y, p.z); }
 
 // Delta-E of move 1, of move 2 and of move 2 after move 1 (FUSED) over the
 // straddle block without its flat far field; every lane returns the sums.
+// A straddle pair adds zero when all its distances, before and after the
+// moves, lie beyond the last bin centre; three nested tests, each exact for
+// the pairs it drops, find the others: (1) each moving atom's images (the
+// atom and its places under the moves) get a sphere, and each chunk of
+// moving atoms a sphere holding those; (2) a chunk pair (moving chunk,
+// fixed chunk) is dropped when their spheres stay `cut` apart; (3) for the
+// kept chunk pairs, a moving atom is dropped against a fixed chunk, and
+// then a pair against its fixed atom, by the same reach.  The pairs left
+// are listed and evaluated 32 at a time, every lane on one pair.
 template <bool FUSED, bool TEX>
 __device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, int m0, int m1,
                        int f0, int f1, float cut, float& s1, float& s2, float& s21,
                        unsigned long long& count) {
   const int lane = threadIdx.x & 31;
-  const int j0 = f0 / kWC, j1 = (f1 - 1) / kWC;
   WMove A1, A2, A21;
   wload_rot(w.maps, A1);
   A2 = A1;
@@ -299,71 +301,137 @@ __device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, 
     wload_rot(w.maps + 12, A2);
     wload_21(w.maps + 24, A1.p, A21);
   }
-  float acc1 = 0.f, acc2 = 0.f, acc21 = 0.f;
   const int nM = m1 - m0;
-  int nq = 0;  // listed items not yet run (the same on every lane)
-  for (int base = 0; base < nM; base += 32) {
-    const int mi = base + lane;
-    ChunkBits b = 0;
-    if (mi < nM) {
-      // the sphere of the moving atom's images, against every chunk
-      const V3<float> xm = w.x(m0 + mi);
-      const V3<float> y1 = wmove_apply(A1, xm);
-      V3<float> o;
-      float r2;
-      if (FUSED) {
-        const V3<float> y2 = wmove_apply(A2, xm), y21 = wmove_apply(A21, xm);
-        o = (xm + y1 + y2 + y21) * 0.25f;
-        r2 = fmaxf(fmaxf(wdist2(xm, o), wdist2(y1, o)), fmaxf(wdist2(y2, o), wdist2(y21, o)));
-      } else {
-        o = (xm + y1) * 0.5f;
-        r2 = fmaxf(wdist2(xm, o), wdist2(y1, o));
-      }
-      const float reach = sqrtf(r2) + cut;
-      for (int j = j0; j <= j1; ++j) {
-        const Pt4<float> q = w.fsph[j];
-        const float lim = reach + q.w;
-        if (wdist2(o, v3<float>(q.x, q.y, q.z)) < lim * lim) b |= ChunkBits(1) << j;
-      }
+  // (1) image spheres of the moving atoms
+  for (int mi = lane; mi < nM; mi += 32) {
+    const V3<float> xm = w.x(m0 + mi);
+    const V3<float> y1 = wmove_apply(A1, xm);
+    V3<float> o;
+    float r2;
+    if (FUSED) {
+      const V3<float> y2 = wmove_apply(A2, xm), y21 = wmove_apply(A21, xm);
+      o = (xm + y1 + y2 + y21) * 0.25f;
+      r2 = fmaxf(fmaxf(wdist2(xm, o), wdist2(y1, o)), fmaxf(wdist2(y2, o), wdist2(y21, o)));
+    } else {
+      o = (xm + y1) * 0.5f;
+      r2 = fmaxf(wdist2(xm, o), wdist2(y1, o));
     }
-    // list this round's items after the ones waiting
-    const int cnt = __popcll(b);
-    int incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
+    Pt4<float> q;
+    q.x = o.x;
+    q.y = o.y;
+    q.z = o.z;
+    q.w = sqrtf(r2);
+    w.isph[mi] = q;
+  }
+  __syncwarp();
+  // ... and of the moving chunks: centred on a middle atom's image sphere,
+  // reaching every image sphere of the chunk
+  const int jm0 = m0 / kWC, nJm = (m1 - 1) / kWC - jm0 + 1;
+  const int jf0 = f0 / kWC, nJf = (f1 - 1) / kWC - jf0 + 1;
+  for (int jj = lane; jj < nJm; jj += 32) {
+    const int a0 = max(kWC * (jm0 + jj), m0) - m0, a1 = min(kWC * (jm0 + jj) + kWC, m1) - m0;
+    const V3<float> c = wc(w.isph[(a0 + a1 - 1) >> 1]);
+    float R = 0.f;
+    for (int q = a0; q < a1; ++q) {
+      const Pt4<float> t = w.isph[q];
+      R = fmaxf(R, sqrtf(wdist2(wc(t), c)) + t.w);
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int pos = nq + incl - cnt;
-    while (b) {
-      const int j = __ffsll((long long)b) - 1;
-      b &= b - 1;
-      w.list[pos++] = (unsigned short)((mi << 6) | j);
+    Pt4<float> q;
+    q.x = c.x;
+    q.y = c.y;
+    q.z = c.z;
+    q.w = R;
+    w.msph[jj] = q;
+  }
+  __syncwarp();
+  float acc1 = 0.f, acc2 = 0.f, acc21 = 0.f;
+  unsigned long long npairs = 0;
+  int np = 0;  // pairs listed and not yet evaluated (the same on every lane)
+  const int ncp = nJm * nJf;
+  for (int cp0 = 0; cp0 < ncp; cp0 += 32) {
+    // (2) 32 chunk pairs
+    const int cp = cp0 + lane;
+    bool keep = false;
+    if (cp < ncp) {
+      const int jm = cp / nJf, jf = cp - jm * nJf;
+      const Pt4<float> a = w.msph[jm], b = w.fsph[jf0 + jf];
+      const float lim = a.w + b.w + cut;
+      keep = wdist2(wc(a), wc(b)) < lim * lim;
     }
-    nq += total;
+    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+    if (!kb) continue;
+    if (keep) w.kp[__popc(kb & ((1u << lane) - 1u))] = (unsigned short)cp;
     __syncwarp();
-    if (nq >= 32) {
-      // run whole batches of 32; the rest waits for the next round
-      const int nrun = nq & ~31;
-      for (int q = lane; q < nrun; q += 32) {
-        const int it = w.list[q];
-        witem<FUSED, TEX>(w, tb, tab_off, L, m0 + (it >> 6), it & 63, f0, f1, A1, A2, A21, acc1,
-                          acc2, acc21, count);
+    const int nit = __popc(kb) * kWC;
+    // (3) their (moving atom, fixed chunk) items, 32 at a time
+    for (int it0 = 0; it0 < nit; it0 += 32) {
+      const int it = it0 + lane;
+      unsigned mask = 0;
+      int m = 0, fb = 0;
+      if (it < nit) {
+        const int cpk = w.kp[it / kWC];
+        const int jm = cpk / nJf, J = jf0 + (cpk - jm * nJf);
+        m = kWC * (jm0 + jm) + it % kWC;
+        if (m >= m0 && m < m1) {
+          const Pt4<float> t = w.isph[m - m0], b = w.fsph[J];
+          const float reach = t.w + cut, lim = reach + b.w;
+          const V3<float> o = wc(t);
+          if (wdist2(o, wc(b)) < lim * lim) {
+            fb = max(kWC * J, f0);
+            const int fe = min(kWC * J + kWC, f1);
+            const float r2 = reach * reach;
+            for (int f = fb; f < fe; ++f)
+              if (wdist2(w.x(f), o) < r2) mask |= 1u << (f - fb);
+          }
+        }
       }
-      const int rem = nq - nrun;
-      const unsigned short v = lane < rem ? w.list[nrun + lane] : (unsigned short)0;
+      const int cnt = __popc(mask);
+      int incl = cnt;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      int pos = np + incl - cnt;
+      while (mask) {
+        const int q = __ffs(mask) - 1;
+        mask &= mask - 1;
+        w.plist[pos++] = ((unsigned)m << 16) | (unsigned)(fb + q);
+      }
+      np += total;
       __syncwarp();
-      if (lane < rem) w.list[lane] = v;
-      __syncwarp();
-      nq = rem;
+      if (np >= kBatch) {
+        // evaluate whole batches; the rest waits
+        const int nrun = np - np % kBatch;
+        for (int q = lane; q < nrun; q += 32) {
+          const unsigned e = w.plist[q];
+          wpair<FUSED, TEX>(w, tb, tab_off, L, (int)(e >> 16), (int)(e & 0xffffu), A1, A2, A21,
+                            acc1, acc2, acc21);
+        }
+        npairs += (unsigned long long)(nrun >> 5);
+        // move the rest (< kBatch pairs) to the front: read all, then write
+        const int rem = np - nrun;
+        unsigned v[kBatch / 32];
+#pragma unroll
+        for (int r = 0; r < kBatch / 32; ++r)
+          v[r] = lane + 32 * r < rem ? w.plist[nrun + lane + 32 * r] : 0u;
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < kBatch / 32; ++r)
+          if (lane + 32 * r < rem) w.plist[lane + 32 * r] = v[r];
+        __syncwarp();
+        np = rem;
+      }
     }
   }
-  if (lane < nq) {
-    const int it = w.list[lane];
-    witem<FUSED, TEX>(w, tb, tab_off, L, m0 + (it >> 6), it & 63, f0, f1, A1, A2, A21, acc1, acc2,
-                      acc21, count);
+  for (int q = lane; q < np; q += 32) {
+    const unsigned e = w.plist[q];
+    wpair<FUSED, TEX>(w, tb, tab_off, L, (int)(e >> 16), (int)(e & 0xffffu), A1, A2, A21, acc1,
+                      acc2, acc21);
+    npairs += 1;
   }
+  count += npairs * (FUSED ? 4 : 2);
   s1 = wsum(acc1);
   s2 = wsum(acc2);
   s21 = wsum(acc21);
