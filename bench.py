@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--global-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="global sweeps: 0 tuned, 1 chains of a CTA in lock-step, "
                          "2 one warp per chain")
+    ap.add_argument("--warps-per-chain", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="chain-group kernel: warps per chain (0 = tuned)")
     ap.add_argument("--clocks-csv", default="",
                     help="keep the nvidia-smi clock samples of the timed region in this file "
                          "(default: a temporary file, removed after it is summarised)")
@@ -381,9 +383,9 @@ def run_schemes():
 
 def run_forms(name=WORKLOAD):
     """The batched FP32 form against the plain FP64 form (one chain per
-    launch) and the batched FP64 form on the same GPU: proposals/s of one AMH
-    cycle of the workload's schedule, and the FP32 form's end energies
-    against the FP64 form's energies of the same states."""
+    launch) on the same GPU: proposals/s of one AMH cycle of the workload's
+    schedule, and the batched FP32 form's end energies against the FP64
+    form's energies (FP64 G(s), FP64 terms) of the same states."""
     import torch
     from paper_2211_03193_gb300 import _amh, synth
     from paper_2211_03193_gb300.sampler import Sampler
@@ -394,7 +396,7 @@ def run_forms(name=WORKLOAD):
     sched = schedule_for(w, seed=1)
     ends = {}
     for label, chains, prec in (("fp32_batched_%d" % nch, nch, 32), ("fp32_one_chain", 1, 32),
-                                ("fp64_one_chain", 1, 64), ("fp64_batched_%d" % nch, nch, 64)):
+                                ("fp64_one_chain", 1, 64)):
         tors = synth.random_torsions(chains, L, seed=w["start_seed"])
         stream = torch.cuda.Stream()
         with Sampler(prot, chains, tors, precision=prec, stream=stream) as s:
@@ -635,7 +637,7 @@ def run_ours(args):
                    chains_per_cta=args.chains_per_cta, threads_per_cta=args.threads,
                    stage_table=args.stage, table_texture=args.texture, far_pairs=args.far_pairs,
                    local_chains_per_cta=args.local_chains_per_cta, local_threads=args.local_threads,
-                   global_kernel=args.global_kernel)
+                   global_kernel=args.global_kernel, warps_per_chain=args.warps_per_chain)
     # a context for the gradient pass only (fixed launch shape: no autotuning)
     gsamp = Sampler(prot, 1, tors[:1], precision=w["precision"], stream=aux, chains_per_cta=1,
                     threads_per_cta=128)
@@ -781,8 +783,8 @@ def run_ours(args):
              (", table entries through the texture path" if args.texture != 2
               else ", table entries through L1 loads"))
     if K == 2:
-        kname = "gwarp_kernel<%s> (global sweep, one warp per chain, %d chains per CTA%s)" % (
-            "true" if args.texture != 2 else "false", C, fetch)
+        kname = "gwarp_kernel<%s> (global sweep, chain groups of %d warps, %d chains per CTA%s)" % (
+            "true" if args.texture != 2 else "false", thr // (32 * C), C, fetch)
     else:
         kname = "global_kernel<float,%d,%s> (global sweep, %d threads/CTA%s)" % (
             C, "true" if D else "false", thr, fetch)
@@ -817,8 +819,8 @@ def run_ours(args):
                       "(256 MB write); the %.1f MB table is read from L2 within a step "
                       "(L2: 129 MB)" % (tab_mb,),
                       "chains_per_cta": C, "threads_per_cta": thr, "stage_depth": D,
-                      "global_kernel": "one warp per chain" if K == 2 else "chains of a CTA "
-                                       "in lock-step",
+                      "global_kernel": ("chain groups of %d warps" % (thr // (32 * C))) if K == 2
+                                       else "chains of a CTA in lock-step",
                       "gradient": "dV/ds of all %d states once per step (one amh_grad launch); %s" % (
                           chains, "on a second stream beside the global sweep, over the states "
                           "that ended the previous step" if args.overlap else

@@ -111,12 +111,16 @@ typedef struct {
   int global_kernel;       /* global sweeps: 0 = chosen by the autotuner among
                               both kernels (the CTA kernel if chains_per_cta is
                               set); 1 = the CTA kernel (chains_per_cta chains
-                              of a CTA in lock-step); 2 = one warp per chain
-                              (chains_per_cta = chains, i.e. warps, per CTA:
-                              0 = tuned, 1, 2, 4 or 8), which needs precision
-                              32, the far-field skip (far_pairs 0, L <= 768)
-                              and no staging, else AMH_EINVAL.  Both kernels
-                              compute the same proposals and decisions. */
+                              of a CTA in lock-step); 2 = chain groups: each
+                              chain on warps_per_chain warps of its own, which
+                              meet at their own barrier (chains_per_cta chains
+                              per CTA: 0 = tuned, 1, 2, 4 or 8, at most 8
+                              warps per CTA), which needs precision 32, the
+                              far-field skip (far_pairs 0, L <= 768) and no
+                              staging, else AMH_EINVAL.  Both kernels compute
+                              the same proposals and decisions. */
+  int warps_per_chain;     /* chain groups: 0 = tuned (1 with a fixed
+                              chains_per_cta), 1, 2 or 4 */
 } amh_options;
 
 /* One proposal record (traced chains only), 32 bytes. */
@@ -327,8 +331,8 @@ const char* amh_last_error(const amh_ctx* ctx);
 
 /* Launch shape of the global sweeps (after tuning): chains per CTA, threads
  * per CTA, staging-ring depth (0 = table rows read through L1) and kernel
- * (1 = chains of a CTA in lock-step, 2 = one warp per chain); any pointer
- * may be NULL. */
+ * (1 = chains of a CTA in lock-step, 2 = chain groups, threads / (32 chains)
+ * warps per chain); any pointer may be NULL. */
 amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per_cta,
                              int* stage_depth, int* kernel);
 

@@ -36,7 +36,7 @@ class amh_options(ctypes.Structure):
                 ("far_pairs", ctypes.c_int), ("local_chains_per_cta", ctypes.c_int),
                 ("local_threads", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("keep_coords", ctypes.c_int), ("wait_test", ctypes.c_int),
-                ("global_kernel", ctypes.c_int)]
+                ("global_kernel", ctypes.c_int), ("warps_per_chain", ctypes.c_int)]
 
 
 class amh_trace_rec(ctypes.Structure):
@@ -228,7 +228,7 @@ def amh_philox(seed, chain, t0, stream, count):
 
 def amh_launch_config(ctx):
     """(chains per CTA, threads per CTA, staging depth, kernel: 1 CTA lock-step,
-    2 warp per chain) of the global sweeps."""
+    2 chain groups) of the global sweeps."""
     c, t, d, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(load().amh_launch_config(ctx, ctypes.byref(c), ctypes.byref(t), ctypes.byref(d),
                                     ctypes.byref(k)), ctx)

@@ -51,9 +51,9 @@ struct amh_ctx {
   long long* trace_count = nullptr;
   // launch configuration
   int C = 8, threads = 256, grid_global = 1;
-  // one warp per chain (FP32 far-field kernel): chains (warps) per CTA and grid
+  // chain groups (FP32 far-field kernel): chains per CTA, warps per chain, grid
   bool use_warp = false;
-  int warpW = 4, grid_warp = 1;
+  int warpW = 4, warpG = 1, grid_warp = 1;
   GroupDev* wgroups_d = nullptr;  // one chain per group
   int nwgroups = 0;
   int stage_depth = 0;  // > 0: global sweeps stage table rows through shared memory
@@ -337,17 +337,18 @@ bool warp_applies(const amh_ctx* ctx) {
          ctx->Lmax <= kMaxChunks * kPairChunk && ctx->opt.global_kernel != 1;
 }
 
-amh_status configure_warp(amh_ctx* ctx, int W) {
-  const size_t sm = gwarp_smem_bytes(ctx->Lmax, W);
-  if (sm > ctx->smem_optin - kStaticSmemMargin)
+amh_status configure_warp(amh_ctx* ctx, int W, int G) {
+  const size_t sm = gwarp_smem_bytes(ctx->Lmax, W, G);
+  if (sm > ctx->smem_optin - kStaticSmemMargin || W * G > 8)
     return set_err(ctx, AMH_EINVAL, "shared memory for this many chains per CTA does not fit");
   if (!ctx->wgroups_d) {
     amh_status st = upload_groups(ctx, make_groups(ctx, 1), &ctx->wgroups_d, &ctx->nwgroups);
     if (st) return st;
   }
   int per_sm = 1;
-  CK(ctx, gwarp_occupancy(W, sm, &per_sm));
+  CK(ctx, gwarp_occupancy(W, G, sm, &per_sm));
   ctx->warpW = W;
+  ctx->warpG = G;
   const int ctas = (ctx->nwgroups + W - 1) / W;
   ctx->grid_warp = std::max(1, std::min(ctas, ctx->sm_count * std::max(per_sm, 1)));
   return AMH_OK;
@@ -414,8 +415,8 @@ amh_status autotune(amh_ctx* ctx) {
       for (int c = 0; c < ctx->nch[p]; ++c) tstart[seg][ctx->prot_h[p].chain0 + c] = at;
     }
   }
-  // the warp-per-chain kernel: chains (warps) per CTA
-  int bestW = 0;
+  // the chain-group kernel: chains per CTA and warps per chain
+  int bestW = 0, bestG = 1;
   float best_warp_ms = 1e30f;
   auto time_runs = [&](auto launch) -> amh_status {
     float ms_sum = 0.f;
@@ -458,20 +459,27 @@ amh_status autotune(amh_ctx* ctx) {
   if constexpr (sizeof(R) == 4) {
     if (warp_applies(ctx)) {
       const int candW[4] = {1, 2, 4, 8};
-      for (int W : candW) {
-        if (gwarp_smem_bytes(ctx->Lmax, W) > ctx->smem_optin - kStaticSmemMargin) continue;
-        amh_status st = configure_warp(ctx, W);
-        if (st) return st;
-        st = time_runs([&](const SweepArgs<R>& a0) {
-          SweepArgs<R> a = a0;
-          a.groups = ctx->wgroups_d;
-          a.ngroups = ctx->nwgroups;
-          return launch_gwarp(a, W, ctx->grid_warp, ctx->stream);
-        });
-        if (st) return st;
-        if (last_ms < best_warp_ms) {
-          best_warp_ms = last_ms;
-          bestW = W;
+      const int candG[3] = {1, 2, 4};
+      for (int G : candG) {
+        if (ctx->opt.warps_per_chain && G != ctx->opt.warps_per_chain) continue;
+        for (int W : candW) {
+          if (W * G > 8 ||
+              gwarp_smem_bytes(ctx->Lmax, W, G) > ctx->smem_optin - kStaticSmemMargin)
+            continue;
+          amh_status st = configure_warp(ctx, W, G);
+          if (st) return st;
+          st = time_runs([&](const SweepArgs<R>& a0) {
+            SweepArgs<R> a = a0;
+            a.groups = ctx->wgroups_d;
+            a.ngroups = ctx->nwgroups;
+            return launch_gwarp(a, W, G, ctx->grid_warp, ctx->stream);
+          });
+          if (st) return st;
+          if (last_ms < best_warp_ms) {
+            best_warp_ms = last_ms;
+            bestW = W;
+            bestG = G;
+          }
         }
       }
     }
@@ -514,7 +522,7 @@ amh_status autotune(amh_ctx* ctx) {
   amh_status st = check_err_flag(ctx);
   if (st) return st;
   if (bestW && (best_warp_ms <= best_ms || ctx->opt.global_kernel == 2)) {
-    st = configure_warp(ctx, bestW);
+    st = configure_warp(ctx, bestW, bestG);
     if (st) return st;
     ctx->use_warp = true;
     // energies (and a precision-64 or staged request) still use the CTA kernel
@@ -580,7 +588,8 @@ amh_status init_impl(amh_ctx* ctx, const float* torsions, const double* table) {
   if (ctx->opt.chains_per_cta == 0) {
     st = autotune<R>(ctx);
   } else if (ctx->opt.global_kernel == 2) {
-    st = configure_warp(ctx, ctx->opt.chains_per_cta);
+    st = configure_warp(ctx, ctx->opt.chains_per_cta,
+                        ctx->opt.warps_per_chain ? ctx->opt.warps_per_chain : 1);
     if (st) return st;
     ctx->use_warp = true;
     st = configure_global<R>(ctx, 1, 128, 0);  // the energy kernel's shape
@@ -630,7 +639,7 @@ amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma
       if (ctx->use_warp) {
         a.groups = ctx->wgroups_d;
         a.ngroups = ctx->nwgroups;
-        CK(ctx, launch_gwarp(a, ctx->warpW, ctx->grid_warp, ctx->stream));
+        CK(ctx, launch_gwarp(a, ctx->warpW, ctx->warpG, ctx->grid_warp, ctx->stream));
         return AMH_OK;
       }
     }
@@ -730,6 +739,7 @@ void amh_options_default(amh_options* opt) {
   opt->keep_coords = 0;
   opt->wait_test = 0;
   opt->global_kernel = 0;
+  opt->warps_per_chain = 0;
 }
 
 amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chains_per_protein,
@@ -774,6 +784,11 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   if (o.wait_test < 0) return set_err(nullptr, AMH_EINVAL, "wait_test must be >= 0");
   if (o.global_kernel < 0 || o.global_kernel > 2)
     return set_err(nullptr, AMH_EINVAL, "global_kernel must be 0, 1 or 2");
+  if (o.warps_per_chain != 0 && o.warps_per_chain != 1 && o.warps_per_chain != 2 &&
+      o.warps_per_chain != 4)
+    return set_err(nullptr, AMH_EINVAL, "warps_per_chain must be 0, 1, 2 or 4");
+  if (o.global_kernel == 2 && o.chains_per_cta * (o.warps_per_chain ? o.warps_per_chain : 1) > 8)
+    return set_err(nullptr, AMH_EINVAL, "at most 8 warps per CTA");
   if (o.global_kernel == 2 &&
       (o.precision != 32 || o.far_pairs != 0 || o.stage_table == 1 || o.threads_per_cta != 0))
     return set_err(nullptr, AMH_EINVAL,
@@ -1262,7 +1277,7 @@ amh_status amh_launch_config(amh_ctx* ctx, int* chains_per_cta, int* threads_per
                              int* stage_depth, int* kernel) {
   if (!ctx) return AMH_ESTATE;
   if (chains_per_cta) *chains_per_cta = ctx->use_warp ? ctx->warpW : ctx->C;
-  if (threads_per_cta) *threads_per_cta = ctx->use_warp ? 32 * ctx->warpW : ctx->threads;
+  if (threads_per_cta) *threads_per_cta = ctx->use_warp ? 32 * ctx->warpW * ctx->warpG : ctx->threads;
   if (stage_depth) *stage_depth = ctx->use_warp ? 0 : ctx->stage_depth;
   if (kernel) *kernel = ctx->use_warp ? 2 : 1;
   return AMH_OK;

@@ -481,6 +481,53 @@ __device__ void build_chains_scan(const Geom<double>& g, const double* kb, int L
   }
 }
 
+// The same build for one chain by nt threads (a multiple of 32; this one is
+// t), whose warps meet at sync(): scratch holds nt/32 * 12 doubles.
+template <class TH, class EMIT, class SYNC>
+__device__ void build_chain_group(const Geom<double>& g, const double* kb, int L, int t, int nt,
+                                  TH theta, EMIT emit, double* scratch, SYNC sync) {
+  const int lane = t & 31, wi = t >> 5, wpc = nt >> 5;
+  const CanonicalResidue<double> cr = canonical_residue(g);
+  const int nb = (L + nt - 1) / nt;
+  const int r0 = min(L, t * nb), r1 = min(L, r0 + nb);
+  Aff<double> agg = identity_map<double>();
+  for (int i = max(r0, 1); i < r1; ++i)
+    agg = compose(agg, residue_step_basis(kb, theta(2 * i - 1), theta(2 * i)));
+  for (int off = 1; off < 32; off <<= 1) {
+    const Aff<double> o = shfl_up_aff(agg, off, 32);
+    if (lane >= off) agg = compose(o, agg);
+  }
+  Aff<double> excl = shfl_up_aff(agg, 1, 32);
+  if (lane == 0) excl = identity_map<double>();
+  if (wpc > 1) {
+    double* tot = scratch + (size_t)wi * 12;
+    if (lane == 31) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) tot[q] = agg.m[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) tot[9 + q] = agg.t[q];
+    }
+    sync();
+    Aff<double> pre = identity_map<double>();
+    for (int w = 0; w < wi; ++w) {
+      const double* tw = scratch + (size_t)w * 12;
+      Aff<double> A;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) A.m[q] = tw[q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) A.t[q] = tw[9 + q];
+      pre = compose(pre, A);
+    }
+    excl = compose(pre, excl);
+    sync();
+  }
+  Aff<double> P = excl;
+  for (int i = r0; i < r1; ++i) {
+    if (i >= 1) P = compose(P, residue_step_basis(kb, theta(2 * i - 1), theta(2 * i)));
+    emit(i, apply(P, cr.N), apply(P, cr.CA), apply(P, cr.C), apply(P, cr.CB));
+  }
+}
+
 // ------------------------------------------------------------------ table
 // Pair term of Eq. 5: -ln p interpolated linearly between evenly spaced bin
 // centres c_j = c0 + j w, flat outside [c_0, c_{B-1}].  Each row holds one

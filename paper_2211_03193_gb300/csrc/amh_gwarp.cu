@@ -1,30 +1,30 @@
-// amh_gwarp.cu -- global Metropolis sweeps (Eqs. 1-3, Alg. 1 first loop),
-// one warp per chain, FP32 with the flat far field skipped.
+// amh_gwarp.cu -- global Metropolis sweeps (Eqs. 1-3, Alg. 1 first loop)
+// by chain groups: G warps (1, 2 or 4) per chain, FP32, flat far field
+// skipped.
 //
-// Each warp takes chains from the work queue and runs a chain's proposals
-// on its own: every step is warp-synchronous (shuffles and __syncwarp, no
-// CTA barrier), so a warp waiting on a map, a sphere or a table fetch holds
-// up nothing but itself and the SM issues the other warps' work meanwhile.
-// A CTA is only a set of such warps sharing the residue-transform basis.
+// A CTA holds S chain slots of G warps each.  A slot takes chains from the
+// work queue and runs a chain's proposals on its own: its warps meet at a
+// named barrier of their own (a warp alone at __syncwarp), never at a
+// CTA-wide one, so a slot waiting on a map, a sphere or a table fetch holds
+// up no other chain.  With G = 2 the 1024 chains of the L = 300 workload
+// are resident at once.
 //
 // Per proposal (the pair 2i-1, 2i = psi_{i-1}, phi_i shares the pivot
-// p = i and is scored in one pass, as in the CTA kernel): lanes 0-2 form
-// the rigid maps A1, A2 and A21 of the moving side (the side of the pivot
-// with fewer residues, Sec. 2.4 step 2); the fixed side's C-betas are cut
-// into absolute chunks of kPairChunk atoms with bounding spheres; each lane
-// takes moving atoms and tests their images' sphere against every chunk;
-// the (moving atom, chunk) items whose spheres come within the last bin
-// centre (plus a rounding margin) are listed and run through the pair loop
-// of Eq. 5, the rest add exactly zero (their terms are the flat last bin
-// before and after the move).  The Metropolis test of Eq. 1 is taken by
-// every lane alike from the warp's butterfly sums.
+// p = i and is scored in one pass, as in the CTA kernel): lanes 0-2 of the
+// slot's first warp form the rigid maps A1, A2 and A21 of the moving side
+// (the side of the pivot with fewer residues, Sec. 2.4 step 2); the far field
+// is dropped by three nested exact tests (see wblock), the surviving pairs of
+// Eq. 5 are evaluated, each warp on its share of the chunk pairs, and the
+// Metropolis test of Eq. 1 is taken by every thread alike from the warps'
+// sums added in a fixed order.
 //
-// Chunk spheres are kept across proposals: chunk j remembers the atom range
-// [lo, hi) that has not moved since its sphere was computed (a commit of the
-// moving side [m0, m1) removes that range), and a sphere is recomputed only
-// when a proposal's fixed part of the chunk is not inside it.  Within a
-// sweep the fixed side is [p, L) while p <= L/2 and [0, p) after, so most
-// spheres are computed once or twice per sweep.
+// The fixed side's C-betas are cut into absolute chunks of kPairChunk atoms
+// with bounding spheres that are kept across proposals: chunk j remembers
+// the atom range [lo, hi) that has not moved since its sphere was computed
+// (a commit of the moving side [m0, m1) removes that range), and a sphere is
+// recomputed only when a proposal's fixed part of the chunk is not inside
+// it.  Within a sweep the fixed side is [p, L) while p <= L/2 and [0, p)
+// after, so most spheres are computed once or twice per sweep.
 #include "amh_internal.h"
 
 namespace amh {
@@ -40,11 +40,15 @@ __host__ __device__ inline size_t wal(size_t x) { return (x + 15) & ~size_t(15);
 // Shared memory of one warp (one chain of up to Lmax residues).
 constexpr int kBatch = 32;  // pairs evaluated at a time: one per lane
 constexpr int kPairCap = 32 * kWC + kBatch;  // one round of 32 items of kWC pairs plus a partial batch
+constexpr int kMaxG = 4;                     // warps per chain at most
 
+// Shared memory of one chain slot (a chain of up to Lmax residues, G warps):
+// the chain's state, then each warp's pair lists.
 struct WLayout {
-  size_t cb, fsph, msph, isph, maps, theta, bb, draws, clean, plist, kp, total;
+  size_t cb, fsph, msph, isph, maps, theta, bb, draws, clean, part, dpart, scan, misc;
+  size_t warp0, warp_bytes, plist, kp, total;
   int nJ;
-  __host__ __device__ explicit WLayout(int Lmax) {
+  __host__ __device__ WLayout(int Lmax, int G) {
     nJ = (Lmax + kWC - 1) / kWC;
     size_t o = 0;
     cb = o;    o = wal(o + sizeof(Pt4<float>) * (size_t)Lmax);
@@ -56,8 +60,15 @@ struct WLayout {
     bb = o;    o = wal(o + sizeof(float) * 9 * (size_t)Lmax);
     draws = o; o = wal(o + sizeof(float) * 2 * kWDraw);
     clean = o; o = wal(o + sizeof(int) * (size_t)nJ);
-    plist = o; o = wal(o + sizeof(unsigned) * (size_t)kPairCap);
-    kp = o;    o = wal(o + sizeof(unsigned short) * 32);
+    part = o;  o = wal(o + sizeof(float) * 4 * kMaxG);
+    dpart = o; o = wal(o + sizeof(double) * kMaxG);
+    scan = o;  o = wal(o + sizeof(double) * 12 * kMaxG);
+    misc = o;  o = wal(o + sizeof(int) * 4);
+    warp0 = o;
+    plist = 0;
+    kp = wal(sizeof(unsigned) * kPairCap);
+    warp_bytes = wal(kp + sizeof(unsigned short) * 32);
+    o += (size_t)G * warp_bytes;
     total = (o + 127) & ~size_t(127);
   }
 };
@@ -72,9 +83,13 @@ struct WShm {
   float* bb;             // [i][v][xyz]: v 0 CA_i, 1 unit N_i -> CA_i, 2 unit CA_i -> C_i
   float* draws;          // [kWDraw][2]: (z, ln u)
   int* clean;            // [chunk] lo | hi << 16: atoms unmoved since the sphere was made
-  unsigned* plist;       // pairs within reach, (moving atom << 16 | fixed atom)
-  unsigned short* kp;    // chunk pairs within reach, of one round
-  __device__ WShm(unsigned char* base, const WLayout& l) {
+  float* part;           // [warp][4] the warps' Delta-E sums
+  double* dpart;         // [warp] the warps' energy sums
+  double* scan;          // [warp][12] the chain build's warp totals
+  int* misc;             // [0] the slot's chain (queue index), [1] best-state flag
+  unsigned* plist;       // this warp's pairs within reach, (moving atom << 16 | fixed atom)
+  unsigned short* kp;    // this warp's chunk pairs within reach, of one round
+  __device__ WShm(unsigned char* base, const WLayout& l, int g) {
     cb = (Pt4<float>*)(base + l.cb);
     fsph = (Pt4<float>*)(base + l.fsph);
     msph = (Pt4<float>*)(base + l.msph);
@@ -84,8 +99,13 @@ struct WShm {
     bb = (float*)(base + l.bb);
     draws = (float*)(base + l.draws);
     clean = (int*)(base + l.clean);
-    plist = (unsigned*)(base + l.plist);
-    kp = (unsigned short*)(base + l.kp);
+    part = (float*)(base + l.part);
+    dpart = (double*)(base + l.dpart);
+    scan = (double*)(base + l.scan);
+    misc = (int*)(base + l.misc);
+    unsigned char* wb = base + l.warp0 + (size_t)g * l.warp_bytes;
+    plist = (unsigned*)(wb + l.plist);
+    kp = (unsigned short*)(wb + l.kp);
   }
   __device__ V3<float> x(int i) const {
     const Pt4<float> p = cb[i];
@@ -108,6 +128,18 @@ struct WShm {
     q[0] = a.x;
     q[1] = a.y;
     q[2] = a.z;
+  }
+};
+
+// The threads of one chain slot: t in [0, nt), warp g of G, and the slot's
+// meeting point (its own named barrier, or __syncwarp for one warp).
+struct Grp {
+  int t, nt, g, G, lane, bar;
+  __device__ void sync() const {
+    if (G == 1)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
   }
 };
 
@@ -192,31 +224,31 @@ __device__ __forceinline__ double wsumd(double v) {
   return v;
 }
 
-// G(s) of the warp's chain in FP64 (the warp's parallel scan of residue
-// transforms), stored in FP32; every chunk sphere becomes stale.
-__device__ void wrebuild(WShm& w, const Geom<double>& g, const double* kb, int L, int nJ) {
-  __syncwarp();
-  build_chains_scan(
-      g, kb, L, 1, [&](int, int k) { return (double)w.theta[k]; },
-      [&](int, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
+// G(s) of the slot's chain in FP64 (a parallel scan of residue transforms
+// over the slot's threads), stored in FP32; every chunk sphere becomes stale.
+__device__ void wrebuild(WShm& w, const Grp& q, const Geom<double>& g, const double* kb, int L,
+                         int nJ) {
+  q.sync();
+  build_chain_group(
+      g, kb, L, q.t, q.nt, [&](int k) { return (double)w.theta[k]; },
+      [&](int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
         w.set_axis(i, 0, v3<float>((float)CA.x, (float)CA.y, (float)CA.z));
         const V3<double> u1 = unit(CA - N), u2 = unit(Cc - CA);
         w.set_axis(i, 1, v3<float>((float)u1.x, (float)u1.y, (float)u1.z));
         w.set_axis(i, 2, v3<float>((float)u2.x, (float)u2.y, (float)u2.z));
         w.set_x(i, v3<float>((float)CB.x, (float)CB.y, (float)CB.z));
       },
-      nullptr, nullptr, 32);
-  for (int j = threadIdx.x & 31; j < nJ; j += 32) w.clean[j] = 0;
-  __syncwarp();
+      w.scan, [&]() { q.sync(); });
+  for (int j = q.t; j < nJ; j += q.nt) w.clean[j] = 0;
+  q.sync();
 }
 
 // Bounding spheres of the chunks that hold fixed atoms [f0, f1): a chunk
 // whose fixed part lies inside its unmoved range keeps its sphere, the others
 // get one over the whole chunk (box centre, largest distance).
-__device__ void wspheres(WShm& w, int L, int f0, int f1) {
-  const int lane = threadIdx.x & 31;
+__device__ void wspheres(WShm& w, const Grp& g, int L, int f0, int f1) {
   const int j0 = f0 / kWC, j1 = (f1 - 1) / kWC;
-  for (int j = j0 + lane; j <= j1; j += 32) {
+  for (int j = j0 + g.t; j <= j1; j += g.nt) {
     const int fa = max(kWC * j, f0), fb = min(kWC * j + kWC, f1);
     const int cl = w.clean[j];
     if ((cl & 0xffff) <= fa && fb <= (cl >> 16)) continue;
@@ -230,15 +262,15 @@ __device__ void wspheres(WShm& w, int L, int f0, int f1) {
     const V3<float> o = (lo + hi) * 0.5f;
     float r2 = 0.f;
     for (int f = ca; f < ce; ++f) r2 = fmaxf(r2, wdist2(w.x(f), o));
-    Pt4<float> q;
-    q.x = o.x;
-    q.y = o.y;
-    q.z = o.z;
-    q.w = sqrtf(r2);
-    w.fsph[j] = q;
+    Pt4<float> s;
+    s.x = o.x;
+    s.y = o.y;
+    s.z = o.z;
+    s.w = sqrtf(r2);
+    w.fsph[j] = s;
     w.clean[j] = ca | (ce << 16);
   }
-  __syncwarp();
+  g.sync();
 }
 
 // One straddle pair (moving atom m, fixed atom f): its terms at the current
@@ -289,10 +321,10 @@ __device__ __forceinline__ V3<float> wc(Pt4<float> p) { return v3<float>(p.x, p.
 // then a pair against its fixed atom, by the same reach.  The pairs left
 // are listed and evaluated 32 at a time, every lane on one pair.
 template <bool FUSED, bool TEX>
-__device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, int m0, int m1,
-                       int f0, int f1, float cut, float& s1, float& s2, float& s21,
-                       unsigned long long& count) {
-  const int lane = threadIdx.x & 31;
+__device__ void wblock(WShm& w, const Grp& grp, const Tab<float>& tb, long long tab_off, int L,
+                       int m0, int m1, int f0, int f1, float cut, float& s1, float& s2,
+                       float& s21, unsigned long long& count) {
+  const int lane = grp.lane;
   WMove A1, A2, A21;
   wload_rot(w.maps, A1);
   A2 = A1;
@@ -303,7 +335,7 @@ __device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, 
   }
   const int nM = m1 - m0;
   // (1) image spheres of the moving atoms
-  for (int mi = lane; mi < nM; mi += 32) {
+  for (int mi = grp.t; mi < nM; mi += grp.nt) {
     const V3<float> xm = w.x(m0 + mi);
     const V3<float> y1 = wmove_apply(A1, xm);
     V3<float> o;
@@ -323,12 +355,12 @@ __device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, 
     q.w = sqrtf(r2);
     w.isph[mi] = q;
   }
-  __syncwarp();
+  grp.sync();
   // ... and of the moving chunks: centred on a middle atom's image sphere,
   // reaching every image sphere of the chunk
   const int jm0 = m0 / kWC, nJm = (m1 - 1) / kWC - jm0 + 1;
   const int jf0 = f0 / kWC, nJf = (f1 - 1) / kWC - jf0 + 1;
-  for (int jj = lane; jj < nJm; jj += 32) {
+  for (int jj = grp.t; jj < nJm; jj += grp.nt) {
     const int a0 = max(kWC * (jm0 + jj), m0) - m0, a1 = min(kWC * (jm0 + jj) + kWC, m1) - m0;
     const V3<float> c = wc(w.isph[(a0 + a1 - 1) >> 1]);
     float R = 0.f;
@@ -343,12 +375,14 @@ __device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, 
     q.w = R;
     w.msph[jj] = q;
   }
-  __syncwarp();
+  grp.sync();
+  // (2)-(3) each warp takes every G-th round of 32 chunk pairs, with its own
+  // lists
   float acc1 = 0.f, acc2 = 0.f, acc21 = 0.f;
   unsigned long long npairs = 0;
   int np = 0;  // pairs listed and not yet evaluated (the same on every lane)
   const int ncp = nJm * nJf;
-  for (int cp0 = 0; cp0 < ncp; cp0 += 32) {
+  for (int cp0 = 32 * grp.g; cp0 < ncp; cp0 += 32 * grp.G) {
     // (2) 32 chunk pairs
     const int cp = cp0 + lane;
     bool keep = false;
@@ -432,19 +466,39 @@ __device__ void wblock(WShm& w, const Tab<float>& tb, long long tab_off, int L, 
     npairs += 1;
   }
   count += npairs * (FUSED ? 4 : 2);
-  s1 = wsum(acc1);
-  s2 = wsum(acc2);
-  s21 = wsum(acc21);
+  acc1 = wsum(acc1);
+  acc2 = wsum(acc2);
+  acc21 = wsum(acc21);
+  if (grp.G == 1) {
+    s1 = acc1;
+    s2 = acc2;
+    s21 = acc21;
+    return;
+  }
+  // the warps' sums, added in warp order by every thread
+  if (lane == 0) {
+    w.part[4 * grp.g] = acc1;
+    w.part[4 * grp.g + 1] = acc2;
+    w.part[4 * grp.g + 2] = acc21;
+  }
+  grp.sync();
+  s1 = s2 = s21 = 0.f;
+  for (int h = 0; h < grp.G; ++h) {
+    s1 += w.part[4 * h];
+    s2 += w.part[4 * h + 1];
+    s21 += w.part[4 * h + 2];
+  }
+  grp.sync();
 }
 
-// V of the warp's chain from its current coordinates: FP32 terms, FP64 sums
-// (Eq. 5 over a < b); every lane returns it.
-__device__ double wenergy(const WShm& w, const Tab<float>& tb, long long tab_off, int L) {
-  const int lane = threadIdx.x & 31;
+// V of the slot's chain from its current coordinates: FP32 terms, FP64 sums
+// (Eq. 5 over a < b); every thread returns it.
+__device__ double wenergy(const WShm& w, const Grp& g, const Tab<float>& tb, long long tab_off,
+                          int L) {
   const int nch = (L - 1 + kWC - 1) / kWC;
   const int items = L * nch;
   double acc = 0.0;
-  for (int it = lane; it < items; it += 32) {
+  for (int it = g.t; it < items; it += g.nt) {
     const int a = it / nch, ch = it - a * nch;
     const int b0 = a + 1 + ch * kWC;
     const int b1 = min(L, b0 + kWC);
@@ -455,46 +509,53 @@ __device__ double wenergy(const WShm& w, const Tab<float>& tb, long long tab_off
     for (int b = b0; b < b1; ++b, row += tb.Bp) part += pair_term(row, dist_(xa, w.x(b)), tb);
     acc += (double)part;
   }
-  return wsumd(acc);
+  acc = wsumd(acc);
+  if (g.G == 1) return acc;
+  if (g.lane == 0) w.dpart[g.g] = acc;
+  g.sync();
+  double e = 0.0;
+  for (int h = 0; h < g.G; ++h) e += w.dpart[h];
+  g.sync();
+  return e;
 }
 
 template <bool TEX>
-__device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb, const GroupDev& G,
-                           const ProteinDev& P, int nJ) {
-  const int lane = threadIdx.x & 31;
+__device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, const double* kb,
+                           const GroupDev& G, const ProteinDev& P, int nJ) {
+  const int t = q.t, nt = q.nt;
   const int L = P.L, n = P.n;
   const int chain = G.chain0;
   const long long toff = P.tors0 + (long long)(chain - P.chain0) * n;
-  for (int k = lane; k < n; k += 32) w.theta[k] = a.theta[toff + k];
+  for (int k = t; k < n; k += nt) w.theta[k] = a.theta[toff + k];
   const long long t0 = a.tcount[chain];
   const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
   const double Tc = a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
   const bool traced = chain < a.trace_chains;
   // decisions need Delta-E only and the exit recomputes V from scratch, so
   // the entry and periodic resyncs rebuild the coordinates alone
-  wrebuild(w, a.geom64, kb, L, nJ);
+  wrebuild(w, q, a.geom64, kb, L, nJ);
   long long since = 0, nacc = 0;
   unsigned long long count = 0;
   long long d0 = 0, dend = 0;
   int kn = (int)(t0 % n);
   for (long long j = 0; j < steps;) {
     if (j + 2 > dend) {
-      __syncwarp();
+      q.sync();
       d0 = j;
       dend = j + kWDraw;
-      for (int q = lane; q < kWDraw; q += 32) {
+      for (int r = t; r < kWDraw; r += nt) {
         float z, lnu;
-        normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)(t0 + j + q), 0u),
+        normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)(t0 + j + r), 0u),
                        &z, &lnu);
-        w.draws[2 * q] = z;
-        w.draws[2 * q + 1] = lnu;
+        w.draws[2 * r] = z;
+        w.draws[2 * r + 1] = lnu;
       }
-      __syncwarp();
+      q.sync();
     }
-    const long long t = t0 + j;
+    const long long tp = t0 + j;
     const int k = kn;
     if (since >= a.resync_every || (k == 0 && j > 0)) {
-      wrebuild(w, a.geom64, kb, L, nJ);
+      wrebuild(w, q, a.geom64, kb, L, nJ);
       since = 0;
     }
     const bool fused = (k & 1) && (k + 1 < n) && (j + 1 < steps);
@@ -506,23 +567,23 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
     // three lanes form the maps: lane 0 move 1's A1, lane 1 move 2's A2
     // about its own axis, lane 2 A1 again and then move 2 about its axis as
     // move 1 left it, composed after A1 (the CTA kernel's arithmetic)
-    if (lane == 0 || (lane < 3 && fused)) {
-      const int k1 = lane == 1 ? k + 1 : k;
+    if (t == 0 || (t < 3 && fused)) {
+      const int k1 = t == 1 ? k + 1 : k;
       const float z = w.draws[2 * (j + (k1 - k) - d0)];
       const float lnu = w.draws[2 * (j + (k1 - k) - d0) + 1];
       const float th = w.theta[k1];
       const float thn = propose(th, z, a.sigma, a.lattice_K);
-      if (lane < 2) {
-        w.maps[36 + lane] = thn;
-        w.maps[38 + lane] = lnu;
+      if (t < 2) {
+        w.maps[36 + t] = thn;
+        w.maps[38 + t] = lnu;
       }
       if (!dead) {
         // k1 odd: psi_i about CA_i -> C_i; k1 even: phi_i about N_i -> CA_i
         const int i = k1 >> 1;
         const float d = wrap_angle(thn - th);
         const WMove A = wmove_rotation(w.axis(i, 0), w.axis(i, (k1 & 1) ? 2 : 1), up ? -d : d);
-        if (lane < 2) {
-          wstore(w.maps + 12 * lane, A, A.p);
+        if (t < 2) {
+          wstore(w.maps + 12 * t, A, A.p);
         } else {
           const float z2 = w.draws[2 * (j + 1 - d0)];
           const float th2 = w.theta[k + 1];
@@ -535,37 +596,38 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
         }
       }
     }
-    __syncwarp();
+    q.sync();
     if (dead) {
       // phi_0 and psi_{L-1} move no C-beta: Delta-E = 0, always accepted
       const float thn = w.maps[36], lnu = w.maps[38];
       const int acc = (double)lnu * Tc < -0.0;
-      if (lane == 0) {
+      if (t == 0) {
         if (acc) w.theta[k] = thn;
-        if (traced && t < a.trace_cap) {
+        if (traced && tp < a.trace_cap) {
           TraceRec r;
           r.k = k;
           r.accept = acc;
           r.theta_new = (double)thn;
           r.lnu = (double)lnu;
           r.dE = 0.0;
-          a.trace[(size_t)chain * a.trace_cap + t] = r;
+          a.trace[(size_t)chain * a.trace_cap + tp] = r;
         }
       }
       nacc += acc;
-      __syncwarp();
+      q.sync();
       j += 1;
       since += 1;
       kn = k + 1 < n ? k + 1 : 0;
       continue;
     }
-    wspheres(w, L, f0, f1);
+    wspheres(w, q, L, f0, f1);
     float s1, s2, s21;
     if (fused)
-      wblock<true, TEX>(w, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21, count);
+      wblock<true, TEX>(w, q, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21, count);
     else
-      wblock<false, TEX>(w, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21, count);
-    // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE, taken by every lane
+      wblock<false, TEX>(w, q, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21,
+                         count);
+    // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE, taken by every thread
     const double d1 = s1, d2 = s2, d21 = s21;
     const float thn1 = w.maps[36], lnu1 = w.maps[38];
     const int acc1 = (double)lnu1 * Tc < -d1;
@@ -576,27 +638,27 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
       acc2 = (double)w.maps[39] * Tc < -e2;
       if (acc2) code = acc1 ? 3 : 2;
     }
-    if (lane == 0) {
+    if (t == 0) {
       if (acc1) w.theta[k] = thn1;
-      if (traced && t < a.trace_cap) {
+      if (traced && tp < a.trace_cap) {
         TraceRec r;
         r.k = k;
         r.accept = acc1;
         r.theta_new = (double)thn1;
         r.lnu = (double)lnu1;
         r.dE = d1;
-        a.trace[(size_t)chain * a.trace_cap + t] = r;
+        a.trace[(size_t)chain * a.trace_cap + tp] = r;
       }
       if (fused) {
         if (acc2) w.theta[k + 1] = w.maps[37];
-        if (traced && t + 1 < a.trace_cap) {
+        if (traced && tp + 1 < a.trace_cap) {
           TraceRec r;
           r.k = k + 1;
           r.accept = acc2;
           r.theta_new = (double)w.maps[37];
           r.lnu = (double)w.maps[39];
           r.dE = e2;
-          a.trace[(size_t)chain * a.trace_cap + t + 1] = r;
+          a.trace[(size_t)chain * a.trace_cap + tp + 1] = r;
         }
       }
     }
@@ -612,7 +674,7 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
         wload_21(w.maps + 24, w.maps + 9, A);
       const int per = up ? 1 : 4;
       const int total = (m1 - m0) * per;
-      for (int idx = lane; idx < total; idx += 32) {
+      for (int idx = t; idx < total; idx += nt) {
         const int v = up ? 3 : (idx & 3), i = m0 + (up ? idx : idx >> 2);
         if (v == 0)
           w.set_axis(i, 0, wmove_apply(A, w.axis(i, 0)));
@@ -623,18 +685,18 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
       }
       // the chunks' unmoved ranges lose [m0, m1)
       if (up) {
-        for (int jj = lane; jj <= (p - 1) / kWC; jj += 32) {
+        for (int jj = t; jj <= (p - 1) / kWC; jj += nt) {
           const int cl = w.clean[jj];
           w.clean[jj] = max(cl & 0xffff, p) | (cl & ~0xffff);
         }
       } else {
-        for (int jj = p / kWC + lane; jj < nJ; jj += 32) {
+        for (int jj = p / kWC + t; jj < nJ; jj += nt) {
           const int cl = w.clean[jj];
           w.clean[jj] = (cl & 0xffff) | (min(cl >> 16, p) << 16);
         }
       }
     }
-    __syncwarp();
+    q.sync();
     j += fused ? 2 : 1;
     kn = k + (fused ? 2 : 1);
     if (kn >= n) kn -= n;
@@ -642,10 +704,10 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
   }
   // exit: V from scratch (FP64 sum) of the current coordinates (their drift
   // since the last rebuild is ~1e-5 A)
-  __syncwarp();
-  const double e = wenergy(w, a.tab, P.tab_off, L);
-  int better = 0;
-  if (lane == 0) {
+  q.sync();
+  const double e = wenergy(w, q, a.tab, P.tab_off, L);
+  if (t == 0) {
+    int better = 0;
     if (!(e == e)) atomicOr(a.err, 1);  // NaN energy
     a.E_cur[chain] = e;
     a.tcount[chain] = t0 + steps;
@@ -656,16 +718,18 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
       a.best_E[chain] = e;
       better = 1;
     }
+    w.misc[1] = better;
   }
-  better = __shfl_sync(0xffffffffu, better, 0);
-  for (int k = lane; k < n; k += 32) {
+  q.sync();
+  const int better = w.misc[1];
+  for (int k = t; k < n; k += nt) {
     const float v = w.theta[k];
     a.theta[toff + k] = v;
     if (better) a.best_theta[toff + k] = v;
   }
   if (a.coords) {
     const long long off = 3 * (toff / 2);
-    for (int i = lane; i < L; i += 32) {
+    for (int i = t; i < L; i += nt) {
       const V3<float> x = w.x(i);
       a.coords[off + 3 * i] = x.x;
       a.coords[off + 3 * i + 1] = x.y;
@@ -675,32 +739,41 @@ __device__ void wrun_chain(WShm& w, const SweepArgs<float>& a, const double* kb,
   unsigned long long c = count;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-  if (lane == 0 && a.pair_count && c) atomicAdd(a.pair_count, c);
-  __syncwarp();
+  if (q.lane == 0 && a.pair_count && c) atomicAdd(a.pair_count, c);
+  q.sync();
 }
 
 template <bool TEX>
-__global__ void __launch_bounds__(256) gwarp_kernel(SweepArgs<float> a) {
+__global__ void __launch_bounds__(256) gwarp_kernel(SweepArgs<float> a, int G) {
   extern __shared__ __align__(128) unsigned char smem[];
   double* kb = reinterpret_cast<double*>(smem);
   residue_basis(a.geom64, kb);  // the whole CTA, once
-  const WLayout lay(a.Lmax);
-  WShm w(smem + kKbBytes + (size_t)(threadIdx.x >> 5) * lay.total, lay);
-  const int lane = threadIdx.x & 31;
+  const WLayout lay(a.Lmax, G);
+  const int warp = threadIdx.x >> 5;
+  Grp q;
+  q.G = G;
+  q.nt = 32 * G;
+  q.g = warp % G;
+  q.lane = threadIdx.x & 31;
+  q.t = threadIdx.x % q.nt;
+  q.bar = 1 + warp / G;  // named barrier of the slot (0 is __syncthreads)
+  unsigned char* base = smem + kKbBytes + (size_t)(warp / G) * lay.total;
+  WShm w(base, lay, q.g);
   for (;;) {
-    int g = 0;
-    if (lane == 0) g = atomicAdd(a.queue, 1);
-    g = __shfl_sync(0xffffffffu, g, 0);
+    if (q.t == 0) w.misc[0] = atomicAdd(a.queue, 1);
+    q.sync();
+    const int g = w.misc[0];
+    q.sync();
     if (g >= a.ngroups) break;
-    const GroupDev G = a.groups[g];
-    wrun_chain<TEX>(w, a, kb, G, a.prot[G.protein], lay.nJ);
+    const GroupDev Gd = a.groups[g];
+    wrun_chain<TEX>(w, q, a, kb, Gd, a.prot[Gd.protein], lay.nJ);
   }
 }
 
 }  // namespace
 
-size_t gwarp_smem_bytes(int Lmax, int warps) {
-  return kKbBytes + (size_t)warps * WLayout(Lmax).total;
+size_t gwarp_smem_bytes(int Lmax, int slots, int G) {
+  return kKbBytes + (size_t)slots * WLayout(Lmax, G).total;
 }
 
 cudaError_t gwarp_set_smem(size_t optin) {
@@ -709,17 +782,17 @@ cudaError_t gwarp_set_smem(size_t optin) {
   return allow_dynamic_smem(gwarp_kernel<false>, optin);
 }
 
-cudaError_t gwarp_occupancy(int warps, size_t smem, int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, gwarp_kernel<true>, 32 * warps,
-                                                       smem);
+cudaError_t gwarp_occupancy(int slots, int G, size_t smem, int* per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, gwarp_kernel<true>,
+                                                       32 * G * slots, smem);
 }
 
-cudaError_t launch_gwarp(const SweepArgs<float>& a, int warps, int grid, cudaStream_t st) {
-  const size_t sm = gwarp_smem_bytes(a.Lmax, warps);
+cudaError_t launch_gwarp(const SweepArgs<float>& a, int slots, int G, int grid, cudaStream_t st) {
+  const size_t sm = gwarp_smem_bytes(a.Lmax, slots, G);
   if (a.tab.tex)
-    gwarp_kernel<true><<<grid, 32 * warps, sm, st>>>(a);
+    gwarp_kernel<true><<<grid, 32 * G * slots, sm, st>>>(a, G);
   else
-    gwarp_kernel<false><<<grid, 32 * warps, sm, st>>>(a);
+    gwarp_kernel<false><<<grid, 32 * G * slots, sm, st>>>(a, G);
   return cudaGetLastError();
 }
 

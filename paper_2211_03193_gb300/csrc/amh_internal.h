@@ -101,12 +101,12 @@ cudaError_t global_set_smem(size_t bytes);
 template <class R, int C, bool ST>
 cudaError_t global_occupancy(int threads, size_t smem, int* per_sm);
 
-// Global sweeps with one warp per chain (FP32, far field skipped, no staging):
-// `warps` chains per CTA; groups of one chain each.
-size_t gwarp_smem_bytes(int Lmax, int warps);
+// Global sweeps by chain groups (FP32, far field skipped, no staging): a CTA
+// holds `slots` chains of G warps each (G = 1, 2 or 4); groups of one chain.
+size_t gwarp_smem_bytes(int Lmax, int slots, int G);
 cudaError_t gwarp_set_smem(size_t optin);
-cudaError_t gwarp_occupancy(int warps, size_t smem, int* per_sm);
-cudaError_t launch_gwarp(const SweepArgs<float>& a, int warps, int grid, cudaStream_t st);
+cudaError_t gwarp_occupancy(int slots, int G, size_t smem, int* per_sm);
+cudaError_t launch_gwarp(const SweepArgs<float>& a, int slots, int G, int grid, cudaStream_t st);
 
 // Window C-betas of proposal k (window d) built by the local sweep kernel's
 // window builder from one chain's torsions (device pointer theta, n values),

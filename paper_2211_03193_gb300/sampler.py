@@ -27,7 +27,7 @@ class Sampler:
                  trace_capacity: int = 0, lattice_K: int = 0, stage_table: int = 0,
                  table_texture: int = 0, far_pairs: int = 0, local_chains_per_cta: int = 0,
                  local_threads: int = 0, keep_coords: int = 0, wait_test: int = 0,
-                 global_kernel: int = 0, stream=None):
+                 global_kernel: int = 0, warps_per_chain: int = 0, stream=None):
         if not isinstance(proteins, (list, tuple)):
             proteins = [proteins]
         chains = list(np.atleast_1d(chains).astype(int))
@@ -61,7 +61,7 @@ class Sampler:
                                        local_chains_per_cta=local_chains_per_cta,
                                        local_threads=local_threads, keep_coords=keep_coords,
                                        wait_test=wait_test, global_kernel=global_kernel,
-                                       stream=stream)
+                                       warps_per_chain=warps_per_chain, stream=stream)
         self.ctx = _amh.amh_init(np.array(self.L), np.array(chains), torsions, table, edges, opt)
         self.precision = precision
 

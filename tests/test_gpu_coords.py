@@ -97,7 +97,8 @@ def test_coordinates_after_moves_equal_oracle(amh, orc, precision, C, kernel, L)
     s_orc = tors.astype(np.float64)
     t0 = 0
     with amh.Sampler(prot, chains, tors, precision=precision, keep_coords=1,
-                     resync_every=1 << 30, chains_per_cta=C, global_kernel=kernel) as s:
+                     resync_every=1 << 30, chains_per_cta=C, global_kernel=kernel,
+                     warps_per_chain=2 if kernel == 2 else 0) as s:
         assert s.launch_config()[3] == kernel
         for steps in (n - 1, n // 2 + 1):
             acc = s.sweep(1, 0, 0.8, 10 * DEG, steps, 17)

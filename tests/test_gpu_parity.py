@@ -275,11 +275,12 @@ def test_global_sweeps_teacher_forced(amh, orc, precision, C, stage, threads, te
         assert np.all(bE <= E + 1e-9)
 
 
-@pytest.mark.parametrize("W,tex,L", [(1, 0, 33), (2, 2, 33), (4, 0, 33), (8, 2, 33),
-                                     (4, 0, 150), (2, 2, 151)])
-def test_warp_kernel_teacher_forced(amh, orc, W, tex, L):
-    """The warp-per-chain global sweep (W chains of a CTA, each on its own
-    warp): teacher-forced oracle replay of every chain over a ragged run
+@pytest.mark.parametrize("W,G,tex,L", [(1, 1, 0, 33), (2, 1, 2, 33), (4, 1, 0, 33), (8, 1, 2, 33),
+                                       (4, 2, 0, 33), (2, 4, 2, 33), (1, 2, 0, 150),
+                                       (2, 2, 2, 151), (2, 4, 0, 150), (4, 1, 0, 150)])
+def test_warp_kernel_teacher_forced(amh, orc, W, G, tex, L):
+    """The chain-group global sweep (W chains of a CTA, each on G warps of
+    its own): teacher-forced oracle replay of every chain over a ragged run
     that ends mid-sweep with an odd leftover and crosses sweep boundaries."""
     chains = 11
     prot = synth.make_protein(L, seed=300 + L)
@@ -287,9 +288,10 @@ def test_warp_kernel_teacher_forced(amh, orc, W, tex, L):
     n = 2 * L
     steps = (3 * n + 7) if L < 100 else (n + 5)
     T, sigma, seed = 0.8, 25 * DEG if L < 100 else 10 * DEG, 99
-    with amh.Sampler(prot, chains, tors, global_kernel=2, chains_per_cta=W, table_texture=tex,
-                     trace_chains=chains, trace_capacity=steps, resync_every=50) as s:
-        assert s.launch_config() == (W, 32 * W, 0, 2)
+    with amh.Sampler(prot, chains, tors, global_kernel=2, chains_per_cta=W, warps_per_chain=G,
+                     table_texture=tex, trace_chains=chains, trace_capacity=steps,
+                     resync_every=50) as s:
+        assert s.launch_config() == (W, 32 * W * G, 0, 2)
         acc = s.sweep(1, 0, T, sigma, steps, seed)
         th, E, bE, bt = s.state()
         P = orc.Problem(L, prot.p, prot.edges)
@@ -305,7 +307,7 @@ def test_warp_kernel_teacher_forced(amh, orc, W, tex, L):
             assert abs(E[c] - e_want) <= 1e-5 * abs(e_want)
             assert s.counter(c) == steps
         assert np.all(bE <= E + 1e-9)
-        print("warp kernel W=%d L=%d: flips %d" % (W, L, flips))
+        print("chain groups W=%d G=%d L=%d: flips %d" % (W, G, L, flips))
 
 
 def test_warp_and_cta_kernels_agree(amh):
@@ -319,8 +321,8 @@ def test_warp_and_cta_kernels_agree(amh):
     steps = 2 * n + 1
     T, sigma, seed = 0.5, 8 * DEG, 13
     runs = []
-    for kw in (dict(global_kernel=2, chains_per_cta=4), dict(global_kernel=1, chains_per_cta=2,
-                                                             threads_per_cta=128)):
+    for kw in (dict(global_kernel=2, chains_per_cta=2, warps_per_chain=2),
+               dict(global_kernel=1, chains_per_cta=2, threads_per_cta=128)):
         with amh.Sampler(prot, chains, tors, trace_chains=chains, trace_capacity=steps,
                          **kw) as s:
             s.sweep(1, 0, T, sigma, steps, seed)
@@ -345,7 +347,7 @@ def test_warp_kernel_limits(amh):
     prot = synth.make_protein(20, seed=345)
     tors = synth.random_torsions(2, 20, seed=346)
     for kw in (dict(precision=64), dict(far_pairs=1), dict(stage_table=1),
-               dict(threads_per_cta=128)):
+               dict(threads_per_cta=128), dict(chains_per_cta=4, warps_per_chain=4)):
         with pytest.raises(AmhError):
             amh.Sampler(prot, 2, tors, global_kernel=2, **kw)
     big = synth.make_protein(800, seed=347)
@@ -437,8 +439,8 @@ def test_split_calls_equal_one_call(amh, stage):
     prot = synth.make_protein(L, seed=320)
     tors = synth.random_torsions(chains, L, seed=321)
     outs = []
-    kw = dict(global_kernel=2, chains_per_cta=4) if stage == 0 else dict(chains_per_cta=8,
-                                                                         stage_table=stage)
+    kw = (dict(global_kernel=2, chains_per_cta=2, warps_per_chain=2) if stage == 0
+          else dict(chains_per_cta=8, stage_table=stage))
     for split in ([170], [33, 1, 136], [80, 90]):
         with amh.Sampler(prot, chains, tors, **kw) as s:
             for st in split:
