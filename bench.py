@@ -96,6 +96,8 @@ def parse():
                          "2 one warp per chain")
     ap.add_argument("--warps-per-chain", type=int, default=0, choices=[0, 1, 2, 4],
                     help="chain-group kernel: warps per chain (0 = tuned)")
+    ap.add_argument("--per-sweep-calls", action="store_true",
+                    help="one library call per local sweep instead of one per run of them")
     ap.add_argument("--clocks-csv", default="",
                     help="keep the nvidia-smi clock samples of the timed region in this file "
                          "(default: a temporary file, removed after it is summarised)")
@@ -653,6 +655,7 @@ def run_ours(args):
     G_dev = torch.empty((chains, n), dtype=torch.float32, device="cuda")
     ev = lambda: torch.cuda.Event(enable_timing=True)
     sweep_idx = [0]
+    launches = [0]  # library kernel launches (sweep calls and gradient passes)
 
     def grad_pass():
         _amh.amh_grad(gsamp.ctx, 0, theta_dev, chains, E_dev, G_dev)
@@ -663,9 +666,27 @@ def run_ours(args):
         default) the gradient pass covers the states that ended the previous
         cycle and runs on the second stream beside the global sweep; the
         cycle ends when both are done, and then snapshots its end states."""
-        for j in range(cyc):
+        j = 0
+        while j < cyc:
             s = sweep_idx[0] % w["total_sweeps"]
             mode, T, sigma = sched.params(s)
+            if mode == _amh.AMH_LOCAL and not args.per_sweep_calls:
+                # the run of local sweeps up to the global one: one library call,
+                # each sweep at its own T and sigma
+                Ts, Ss = [], []
+                while j < cyc and len(Ts) < _amh.AMH_MAX_SCHED:
+                    s = sweep_idx[0] % w["total_sweeps"]
+                    m2, T2, sg2 = sched.params(s)
+                    if m2 != _amh.AMH_LOCAL or (Ts and s == 0):
+                        break
+                    Ts.append(T2)
+                    Ss.append(sg2)
+                    sweep_idx[0] += 1
+                    j += 1
+                _amh.amh_sweeps_sched(samp.ctx, mode, w["window"], Ts, Ss, sched.seed, None)
+                launches[0] += 1
+                continue
+            launches[0] += 1
             if mode == _amh.AMH_GLOBAL and args.overlap:
                 go = torch.cuda.Event()
                 go.record(stream)
@@ -684,6 +705,8 @@ def run_ours(args):
             if mode == _amh.AMH_GLOBAL and args.overlap:
                 stream.wait_event(done)
             sweep_idx[0] += 1
+            j += 1
+        launches[0] += 1  # the gradient pass
         _amh.amh_get_state(samp.ctx, theta_dev, None, None, None)
         if not args.overlap:
             go = torch.cuda.Event()
@@ -704,6 +727,7 @@ def run_ours(args):
         dist.barrier()
     step_ms = []
     glob_ev = []
+    launches[0] = 0
     terms0 = samp.pair_terms()  # straddle-pair terms evaluated so far (synchronises)
     with Clocks(local, args.clocks_csv or None) as clk:
         for _ in range(args.steps):
@@ -717,6 +741,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    timed_launches = launches[0]
     terms_glob = (samp.pair_terms() - terms0) / args.steps  # per global sweep, this rank
     total_ms = sum(a.elapsed_time(b_) for a, b_ in step_ms)
     glob_ms = [a.elapsed_time(b_) for a, b_ in glob_ev]
@@ -831,7 +856,7 @@ def run_ours(args):
            "pair_evals_per_s": (evals_glob_launch + ev_loc * chains) * args.steps * world /
                                (total_ms / 1000.0),
            "pair_evals_dense_per_s": evals_step * args.steps * world / (total_ms / 1000.0),
-           "roofline": roof, "gpu_launches": args.steps * (cyc + 1),
+           "roofline": roof, "gpu_launches": timed_launches,
            "best_energy_all_ranks": best_e, "best_rank": best_rank,
            "clocks": clocks, "e2e": e2e, "measured_peaks": mp}
     if not args.no_cpu:

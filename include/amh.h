@@ -218,6 +218,22 @@ amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, dou
                     void* dE_dtheta);
 
 /*
+ * amh_sweeps_sched -- a run of nsweeps whole sweeps in one call (Alg. 1's
+ * inner loop of N_local localized or N_global global sweeps), sweep q of the
+ * run at temperature T[q] and step sigma_rad[q] (the annealing schedule of
+ * Sec. 2.3 / Sec. 3 changes them from sweep to sweep).
+ *   T, sigma_rad   host, [nsweeps] doubles; T[q] > 0.
+ *   1 <= nsweeps <= AMH_MAX_SCHED; every chain's proposal counter must sit
+ *   at a sweep boundary (t a multiple of n), else AMH_EINVAL.
+ * The result equals nsweeps calls of amh_sweeps(.., 1, ..) with those T and
+ * sigma (the same proposals, draws and decisions); accepted_out sums the run.
+ */
+#define AMH_MAX_SCHED 16
+amh_status amh_sweeps_sched(amh_ctx* ctx, int mode, int window, int nsweeps, const double* T,
+                            const double* sigma_rad, unsigned long long seed,
+                            long long* accepted_out);
+
+/*
  * amh_get_state -- copy out the chains' state; any pointer may be NULL.
  *   torsions_out, best_torsions  [sum chains * 2 L] float32 (host or device)
  *   E_out      V as of the last global sweep or amh_energy call [chains];

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libamh.so")
 
 AMH_OK, AMH_EINVAL, AMH_ENOMEM, AMH_ECUDA, AMH_ETIMEOUT, AMH_ESTATE = range(6)
 AMH_LOCAL, AMH_GLOBAL = 0, 1
+AMH_MAX_SCHED = 16  # sweeps of one amh_sweeps_sched call at most (amh.h)
 _STATUS = {0: "AMH_OK", 1: "AMH_EINVAL", 2: "AMH_ENOMEM", 3: "AMH_ECUDA", 4: "AMH_ETIMEOUT",
            5: "AMH_ESTATE"}
 
@@ -68,6 +69,8 @@ def load() -> ctypes.CDLL:
     L.amh_sweep.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                             ctypes.c_longlong, ctypes.c_ulonglong, vp]
     L.amh_sweeps.argtypes = L.amh_sweep.argtypes
+    L.amh_sweeps_sched.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                   ctypes.c_ulonglong, vp]
     L.amh_grad.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]
     L.amh_get_state.argtypes = [vp, vp, vp, vp, vp]
     L.amh_set_state.argtypes = [vp, vp]
@@ -91,7 +94,8 @@ def load() -> ctypes.CDLL:
     for name in ("amh_init", "amh_energy", "amh_sweep", "amh_sweeps", "amh_grad", "amh_get_state",
                  "amh_set_state", "amh_noisy_restart", "amh_get_trace", "amh_counter",
                  "amh_philox", "amh_launch_config", "amh_grad_noalloc", "amh_set_ladder",
-                 "amh_exchange", "amh_pair_terms", "amh_get_coords", "amh_window_coords"):
+                 "amh_exchange", "amh_pair_terms", "amh_get_coords", "amh_window_coords",
+                 "amh_sweeps_sched"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -159,6 +163,17 @@ def amh_sweep(ctx, mode, window, T, sigma_rad, steps, seed, accepted_out=None):
 def amh_sweeps(ctx, mode, window, T, sigma_rad, nsweeps, seed, accepted_out=None):
     _check(load().amh_sweeps(ctx, int(mode), int(window), float(T), float(sigma_rad), int(nsweeps),
                              int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(accepted_out)), ctx)
+
+
+def amh_sweeps_sched(ctx, mode, window, T, sigma_rad, seed, accepted_out=None):
+    """A run of len(T) whole sweeps, sweep q at T[q] and sigma_rad[q]."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    S = np.ascontiguousarray(sigma_rad, dtype=np.float64)
+    if T.shape != S.shape or T.ndim != 1:
+        raise ValueError("T and sigma_rad must be 1-D arrays of one length")
+    _check(load().amh_sweeps_sched(ctx, int(mode), int(window), int(T.shape[0]), T.ctypes.data,
+                                   S.ctypes.data, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                   _ptr(accepted_out)), ctx)
 
 
 def amh_grad(ctx, protein, theta, batch, E_out, dE_dtheta):
@@ -276,4 +291,4 @@ EXPORTED = ["amh_options_default", "amh_init", "amh_energy", "amh_sweep", "amh_s
             "amh_grad", "amh_get_state", "amh_set_state", "amh_noisy_restart", "amh_get_trace",
             "amh_counter", "amh_philox", "amh_last_error", "amh_launch_config", "amh_destroy",
             "amh_grad_noalloc", "amh_set_ladder", "amh_exchange", "amh_pair_terms",
-            "amh_get_coords", "amh_window_coords"]
+            "amh_get_coords", "amh_window_coords", "amh_sweeps_sched"]

@@ -625,10 +625,16 @@ constexpr int kLocalMaxChains = 32;
 
 template <class R>
 amh_status sweep_impl(amh_ctx* ctx, int mode, int window, double T, double sigma, long long steps,
-                      int are_sweeps, unsigned long long seed) {
+                      int are_sweeps, unsigned long long seed, int nsched = 0,
+                      const double* Ts = nullptr, const double* Ss = nullptr) {
   SweepArgs<R> a = make_args<R>(ctx);
   a.T = T;
   a.sigma = (R)sigma;
+  a.nsched = nsched;
+  for (int q = 0; q < nsched; ++q) {
+    a.sched_T[q] = Ts[q];
+    a.sched_sigma[q] = (R)Ss[q];
+  }
   a.seed = seed;
   a.steps = steps;
   a.steps_are_sweeps = are_sweeps;
@@ -946,13 +952,23 @@ amh_status amh_energy(amh_ctx* ctx, double* E_out) {
 
 static amh_status sweep_common(amh_ctx* ctx, int mode, int window, double T, double sigma,
                                long long steps, int are_sweeps, unsigned long long seed,
-                               long long* accepted_out) {
+                               long long* accepted_out, int nsched = 0,
+                               const double* Ts = nullptr, const double* Ss = nullptr) {
   amh_status st = check_ctx(ctx);
   if (st) return st;
   if (mode != AMH_LOCAL && mode != AMH_GLOBAL) return set_err(ctx, AMH_EINVAL, "bad mode");
   if (!(T > 0) || !std::isfinite(T)) return set_err(ctx, AMH_EINVAL, "T must be positive");
   if (!std::isfinite(sigma)) return set_err(ctx, AMH_EINVAL, "sigma must be finite");
   if (steps < 0) return set_err(ctx, AMH_EINVAL, "steps must be >= 0");
+  for (int q = 0; q < nsched; ++q) {
+    if (!(Ts[q] > 0) || !std::isfinite(Ts[q]))
+      return set_err(ctx, AMH_EINVAL, "every T[q] must be positive");
+    if (!std::isfinite(Ss[q])) return set_err(ctx, AMH_EINVAL, "every sigma[q] must be finite");
+  }
+  if (nsched)
+    for (int p = 0; p < ctx->nprot; ++p)
+      if (ctx->t_host[p] % (2LL * ctx->L[p]) != 0)
+        return set_err(ctx, AMH_EINVAL, "a scheduled run starts on a sweep boundary");
   if (mode == AMH_LOCAL) {
     if (window < 0 || window > 64) return set_err(ctx, AMH_EINVAL, "window must be in [0, 64]");
     for (int p = 0; p < ctx->nprot; ++p) {
@@ -963,8 +979,10 @@ static amh_status sweep_common(amh_ctx* ctx, int mode, int window, double T, dou
   }
   if (steps > 0) {
     st = ctx->precision == 64
-             ? sweep_impl<double>(ctx, mode, window, T, sigma, steps, are_sweeps, seed)
-             : sweep_impl<float>(ctx, mode, window, T, sigma, steps, are_sweeps, seed);
+             ? sweep_impl<double>(ctx, mode, window, T, sigma, steps, are_sweeps, seed, nsched,
+                                  Ts, Ss)
+             : sweep_impl<float>(ctx, mode, window, T, sigma, steps, are_sweeps, seed, nsched,
+                                 Ts, Ss);
     if (st) return st;
     if (mode == AMH_GLOBAL) ctx->energy_stale = false;  // every chain ends with V from scratch
   } else {
@@ -988,6 +1006,15 @@ amh_status amh_sweep(amh_ctx* ctx, int mode, int window, double T, double sigma_
 amh_status amh_sweeps(amh_ctx* ctx, int mode, int window, double T, double sigma_rad,
                       long long nsweeps, unsigned long long seed, long long* accepted_out) {
   return sweep_common(ctx, mode, window, T, sigma_rad, nsweeps, 1, seed, accepted_out);
+}
+
+amh_status amh_sweeps_sched(amh_ctx* ctx, int mode, int window, int nsweeps, const double* T,
+                            const double* sigma_rad, unsigned long long seed,
+                            long long* accepted_out) {
+  if (ctx && (nsweeps < 1 || nsweeps > AMH_MAX_SCHED || !T || !sigma_rad))
+    return set_err(ctx, AMH_EINVAL, "need 1 <= nsweeps <= AMH_MAX_SCHED and T, sigma arrays");
+  return sweep_common(ctx, mode, window, ctx ? T[0] : 1.0, ctx ? sigma_rad[0] : 0.0, nsweeps, 1,
+                      seed, accepted_out, nsweeps, T, sigma_rad);
 }
 
 amh_status amh_grad(amh_ctx* ctx, int protein, const void* theta, int batch, double* E_out,

@@ -752,8 +752,9 @@ __device__ void commit_moves(Shm<R, C>& s, int m0, int m1, bool cb_only) {
 // Temperature of chain slot c: T, times its ladder factor under parallel
 // tempering.
 template <class R>
-__device__ __forceinline__ double chain_T(const SweepArgs<R>& a, const ProteinDev& P, int chain) {
-  return a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
+__device__ __forceinline__ double chain_T(const SweepArgs<R>& a, const ProteinDev& P, int chain,
+                                          double T) {
+  return a.ladder ? T * a.ladder[(chain - P.chain0) % a.ladder_K] : T;
 }
 
 template <class R>
@@ -850,6 +851,9 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
   long long d0 = 0, dend = 0;  // proposals [d0, dend) have their draws in s.draws
   int kn = (int)(t0 % n);      // torsion index of proposal t0 + j (kept without a 64-bit modulo)
+  long long sw = 0;            // sweep of the call (scheduled calls start on a sweep boundary)
+  double Tsw = a.T_of(0);
+  R sig = a.sigma_of(0);
   for (long long j = 0; j < steps;) {
     if (j + 2 > dend) {
       // the Philox draws of the next kDraw proposals, by all threads (they
@@ -872,6 +876,11 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     const int k = kn;
     // periodic rebuild, and one at each new sweep inside a call (commits of
     // upstream moves leave torsion axes behind, see commit_moves)
+    if (k == 0 && j > 0 && a.nsched) {
+      ++sw;
+      Tsw = a.T_of(sw);
+      sig = a.sigma_of(sw);
+    }
     if (since >= a.resync_every || (k == 0 && j > 0)) {
       rebuild(s, a, P);
       since = 0;
@@ -900,7 +909,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         const R z = s.draws[2 * (j + (k1 - k) - d0)];
         const R lnu = s.draws[2 * (j + (k1 - k) - d0) + 1];
         const R th = s.theta[k1];
-        const R thn = propose(th, z, a.sigma, a.lattice_K);
+        const R thn = propose(th, z, sig, a.lattice_K);
         if (q < 2) {
           s.thn[q] = thn;
           s.lnu[q] = lnu;
@@ -916,7 +925,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
           } else {
             const R z2 = s.draws[2 * (j + 1 - d0)];
             const R th2 = s.theta[k + 1];
-            const R d2 = wrap_angle(propose(th2, z2, a.sigma, a.lattice_K) - th2);
+            const R d2 = wrap_angle(propose(th2, z2, sig, a.lattice_K) - th2);
             const V3<R> P2 = s.bbv(p, 0, 0), u2 = s.bbv(p, 1, 0);  // phi_p: N_p -> CA_p
             // after move 1 the axis of move 2 has moved with the far side
             const V3<R> P2m = up ? P2 : move_apply(A, P2);
@@ -931,7 +940,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         const int c = threadIdx.x;
         const R z = s.draws[2 * ((j - d0) * C + c)], lnu = s.draws[2 * ((j - d0) * C + c) + 1];
         const R th = s.theta[k * C + c];
-        const R thn = propose(th, z, a.sigma, a.lattice_K);
+        const R thn = propose(th, z, sig, a.lattice_K);
         s.thn[c] = thn;
         s.lnu[c] = lnu;
         if (!dead) {
@@ -945,7 +954,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
             const R z2 = s.draws[2 * ((j + 1 - d0) * C + c)];
             const R lnu2 = s.draws[2 * ((j + 1 - d0) * C + c) + 1];
             const R th2 = s.theta[(k + 1) * C + c];
-            const R thn2 = propose(th2, z2, a.sigma, a.lattice_K);
+            const R thn2 = propose(th2, z2, sig, a.lattice_K);
             s.thn[C + c] = thn2;
             s.lnu[C + c] = lnu2;
             const R d2 = wrap_angle(thn2 - th2);
@@ -968,7 +977,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       if (threadIdx.x < C) {
         const int c = threadIdx.x;
         const int chain = G.chain0 + c;
-        const int acc = (double)s.lnu[c] * chain_T(a, P, chain) < -0.0;
+        const int acc = (double)s.lnu[c] * chain_T(a, P, chain, Tsw) < -0.0;
         if (acc) s.theta[k * C + c] = s.thn[c];
         s.acc[c] += acc;
         put_trace(a, c < G.nchains, chain, t, k, acc, s.thn[c], s.lnu[c], 0.0);
@@ -1049,7 +1058,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
           d21 += pp[2];
         }
       }
-      const double Tc = chain_T(a, P, chain);
+      const double Tc = chain_T(a, P, chain, Tsw);
       // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE (no division)
       const int acc1 = (double)s.lnu[c] * Tc < -d1;
       int code = acc1;

@@ -529,7 +529,10 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
   for (int k = t; k < n; k += nt) w.theta[k] = a.theta[toff + k];
   const long long t0 = a.tcount[chain];
   const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
-  const double Tc = a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
+  const double lad = a.ladder ? a.ladder[(chain - P.chain0) % a.ladder_K] : 1.0;
+  long long sw = 0;  // sweep of the call (scheduled calls start on a sweep boundary)
+  double Tc = a.T_of(0) * lad;
+  float sig = a.sigma_of(0);
   const bool traced = chain < a.trace_chains;
   // decisions need Delta-E only and the exit recomputes V from scratch, so
   // the entry and periodic resyncs rebuild the coordinates alone
@@ -554,6 +557,11 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
     }
     const long long tp = t0 + j;
     const int k = kn;
+    if (k == 0 && j > 0 && a.nsched) {
+      ++sw;
+      Tc = a.T_of(sw) * lad;
+      sig = a.sigma_of(sw);
+    }
     if (since >= a.resync_every || (k == 0 && j > 0)) {
       wrebuild(w, q, a.geom64, kb, L, nJ);
       since = 0;
@@ -572,7 +580,7 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
       const float z = w.draws[2 * (j + (k1 - k) - d0)];
       const float lnu = w.draws[2 * (j + (k1 - k) - d0) + 1];
       const float th = w.theta[k1];
-      const float thn = propose(th, z, a.sigma, a.lattice_K);
+      const float thn = propose(th, z, sig, a.lattice_K);
       if (t < 2) {
         w.maps[36 + t] = thn;
         w.maps[38 + t] = lnu;
@@ -587,7 +595,7 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
         } else {
           const float z2 = w.draws[2 * (j + 1 - d0)];
           const float th2 = w.theta[k + 1];
-          const float d2 = wrap_angle(propose(th2, z2, a.sigma, a.lattice_K) - th2);
+          const float d2 = wrap_angle(propose(th2, z2, sig, a.lattice_K) - th2);
           const V3<float> P2 = w.axis(p, 0), u2 = w.axis(p, 1);  // phi_p: N_p -> CA_p
           const V3<float> P2m = up ? P2 : wmove_apply(A, P2);
           const V3<float> u2m = up ? u2 : wmove_lin(A, u2);

@@ -7,6 +7,7 @@
 #include <string>
 #include <cuda_runtime.h>
 
+#include "amh.h"
 #include "amh_device.cuh"
 
 namespace amh {
@@ -47,6 +48,9 @@ constexpr int kPairChunk = 12;
 using ChunkBits = unsigned long long;
 constexpr int kMaxChunks = 64;
 
+// Sweeps of one scheduled call (amh_sweeps_sched) at most.
+constexpr int kMaxSched = AMH_MAX_SCHED;
+
 template <class R>
 struct SweepArgs {
   const ProteinDev* prot;
@@ -84,6 +88,14 @@ struct SweepArgs {
   int* err;
   R* coords;      // per chain C-betas, 3 values per residue at 3 * (torsion offset / 2), or null
   int wait_test;  // staged sweeps: > 0 = first wait on an empty ring slot, this many tries
+  // a run of whole sweeps with its own T and sigma per sweep (nsched > 0):
+  // sweep q of the call (counted from the call's first proposal, which sits
+  // at a sweep boundary) uses sched_T[q] and sched_sigma[q] instead of T, sigma
+  int nsched;
+  double sched_T[kMaxSched];
+  R sched_sigma[kMaxSched];
+  __device__ __forceinline__ double T_of(long long q) const { return nsched ? sched_T[q] : T; }
+  __device__ __forceinline__ R sigma_of(long long q) const { return nsched ? sched_sigma[q] : sigma; }
 };
 
 // Global sweeps (Eqs. 1-3, Alg. 1 first loop) and full-energy resync.

@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
     const long long nsw = a.steps_are_sweeps ? a.steps : a.steps / n;
     __syncthreads();
     for (long long sw = 0; sw < nsw; ++sw) {
+      const R sig = a.sigma_of(sw);
+      const double Tsw = a.T_of(sw);
       // the sweep's draws, all at once (they depend on the counter only):
       // no Philox on a window's critical path
       for (int idx = tid; idx < n * Gc; idx += nt) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
           const int chain = G.chain0 + c;
           const R z = dr_s[2 * (k * Gc + c)], lnu = dr_s[2 * (k * Gc + c) + 1];
           const R th = th_s[k * Gc + c];
-          const R thn = propose(th, z, a.sigma, a.lattice_K);
+          const R thn = propose(th, z, sig, a.lattice_K);
           const int i = k >> 1;
           const int lo = max(0, i - h), hi = min(L - 1, i + h);
           const int p = (k + 1) >> 1;
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
             }
           }
           const double dE = (double)acc;
-          const double Tc = a.ladder ? a.T * a.ladder[(chain - P.chain0) % a.ladder_K] : a.T;
+          const double Tc = a.ladder ? Tsw * a.ladder[(chain - P.chain0) % a.ladder_K] : Tsw;
           // ln u < -dE / T with T > 0 (FP32 form: in FP32, the precision of dE)
           const int accept = sizeof(R) == 4 ? (float)lnu * (float)Tc < -(float)acc
                                             : (double)lnu * Tc < -dE;

@@ -82,6 +82,12 @@ class Sampler:
         _amh.amh_sweeps(self.ctx, mode, window, T, sigma_rad, nsweeps, seed, acc)
         return acc
 
+    def sweeps_sched(self, mode: int, window: int, T, sigma_rad, seed: int, accepted=True):
+        """A run of len(T) whole sweeps in one call, sweep q at T[q], sigma_rad[q]."""
+        acc = np.zeros(self.n_chains, dtype=np.int64) if accepted else None
+        _amh.amh_sweeps_sched(self.ctx, mode, window, T, sigma_rad, seed, acc)
+        return acc
+
     def state(self):
         th = np.zeros(self.tors_total, dtype=np.float32)
         bt = np.zeros(self.tors_total, dtype=np.float32)
@@ -209,12 +215,43 @@ class Schedule:
         return mode, T, sigma
 
 
+def schedule_runs(sched: Schedule, s0: int, s1: int, limit: int = _amh.AMH_MAX_SCHED):
+    """Sweeps [s0, s1) of the schedule as runs that one library call can take:
+    consecutive sweeps of one mode and window, at most `limit` of them, a
+    run ending where a noisy restart follows.  Yields (mode, window, [s])."""
+    run = []
+    for s in range(s0, s1):
+        mode = sched.params(s)[0]
+        win = sched.window_of(s)
+        if run and (mode, win) != (sched.params(run[0])[0], sched.window_of(run[0])):
+            yield sched.params(run[0])[0], sched.window_of(run[0]), run
+            run = []
+        run.append(s)
+        if len(run) == limit or (sched.noisy_every and (s + 1) % sched.noisy_every == 0):
+            yield mode, win, run
+            run = []
+    if run:
+        yield sched.params(run[0])[0], sched.window_of(run[0]), run
+
+
 def run_schedule(sampler: Sampler, sched: Schedule, s0: int = 0, s1: int | None = None,
                  on_sweep=None):
-    """Run sweeps [s0, s1) of the schedule; returns total accepted per chain."""
+    """Run sweeps [s0, s1) of the schedule; returns total accepted per chain
+    (counted only when on_sweep is given).  Without on_sweep the sweeps go to
+    the library in runs (one call per run of same-mode sweeps, each sweep at
+    its own T and sigma), which gives the same result as one call per sweep."""
     if s1 is None:
         s1 = sched.total_sweeps
     total = np.zeros(sampler.n_chains, dtype=np.int64)
+    if on_sweep is None:
+        for mode, win, run in schedule_runs(sched, s0, s1):
+            Ts = [sched.params(s)[1] for s in run]
+            Ss = [sched.params(s)[2] for s in run]
+            sampler.sweeps_sched(mode, win, Ts, Ss, sched.seed, accepted=False)
+            last = run[-1]
+            if sched.noisy_every and (last + 1) % sched.noisy_every == 0:
+                sampler.noisy_restart(math.radians(sched.noisy_sd_deg), sched.seed * 1000003 + last)
+        return total
     for s in range(s0, s1):
         mode, T, sigma = sched.params(s)
         acc = sampler.sweeps(mode, sched.window_of(s), T, sigma, 1, sched.seed,
@@ -234,16 +271,19 @@ def capture_schedule(sampler: Sampler, sched: Schedule, s0: int, s1: int, stream
     `stream`, which must be the stream the sampler was created with.  Replay
     runs them again on the device; the chains' proposal counters live in
     device memory, so each replay continues where the previous one ended.
-    Capturing runs nothing and counts the sweeps once on the host side."""
+    Capturing runs nothing and counts the sweeps once on the host side.  Runs
+    of same-mode sweeps are captured as one launch each (schedule_runs)."""
     import torch
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
-        for s in range(s0, s1):
-            mode, T, sigma = sched.params(s)
-            _amh.amh_sweeps(sampler.ctx, mode, sched.window_of(s), T, sigma, 1, sched.seed, None)
-            if sched.noisy_every and (s + 1) % sched.noisy_every == 0:
+        for mode, win, run in schedule_runs(sched, s0, s1):
+            Ts = [sched.params(s)[1] for s in run]
+            Ss = [sched.params(s)[2] for s in run]
+            _amh.amh_sweeps_sched(sampler.ctx, mode, win, Ts, Ss, sched.seed, None)
+            last = run[-1]
+            if sched.noisy_every and (last + 1) % sched.noisy_every == 0:
                 _amh.amh_noisy_restart(sampler.ctx, math.radians(sched.noisy_sd_deg),
-                                       sched.seed * 1000003 + s)
+                                       sched.seed * 1000003 + last)
     return g
 
 

@@ -90,6 +90,21 @@ def test_null_context_calls_return_estate(lib):
     lib.amh_destroy(None)
 
 
+def test_binding_constants_match_the_header():
+    from paper_2211_03193_gb300 import _amh
+    src = open(os.path.join(ROOT, "include", "amh.h")).read()
+    m = re.search(r"#define AMH_MAX_SCHED (\d+)", src)
+    assert m and int(m.group(1)) == _amh.AMH_MAX_SCHED
+    m = re.search(r"#define AMH_NOALLOC_MAX_ENTRIES \(1 << (\d+)\)", src)
+    assert m
+
+
+def test_sched_call_refuses_bad_runs_without_a_device(lib):
+    import ctypes as ct
+    T = (ct.c_double * 2)(1.0, 1.0)
+    assert lib.amh_sweeps_sched(None, 1, 0, 2, T, T, 1, None) == 5  # NULL context
+
+
 def test_options_default_far_field_skip_on():
     from paper_2211_03193_gb300 import _amh
     o = _amh.amh_options_default()

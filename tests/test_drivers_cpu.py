@@ -28,6 +28,14 @@ class Recorder:
         self.sweeps_done += nsweeps
         return np.ones(self.n_chains, dtype=np.int64) if accepted else None
 
+    def sweeps_sched(self, mode, window, T, sigma, seed, accepted=True):
+        assert len(T) == len(sigma) <= _amh.AMH_MAX_SCHED
+        for t, sg in zip(T, sigma):
+            self.calls.append(("sweep", mode, window, t, sg, seed))
+        self.calls.append(("run", len(T)))
+        self.sweeps_done += len(T)
+        return np.ones(self.n_chains, dtype=np.int64) * len(T) if accepted else None
+
     def noisy_restart(self, sd, seed):
         self.calls.append(("noisy", sd, seed))
 
@@ -58,6 +66,31 @@ def test_run_schedule_order_windows_and_noisy_restarts():
     assert [c[2] for _, c in noisy] == [5 * 1000003 + 3, 5 * 1000003 + 7]
     assert all(c[1] == math.radians(20.0) for _, c in noisy)
     assert np.array_equal(acc, np.full(3, 9))
+
+
+def test_run_schedule_in_runs_of_one_mode():
+    """Without a per-sweep callback the schedule goes to the library in runs:
+    consecutive sweeps of one mode and window, at most AMH_MAX_SCHED, a run
+    ending before each noisy restart; every sweep keeps its own T and sigma."""
+    sch = Schedule(total_sweeps=40, n_local=18, n_global=2, windows=(8,), noisy_every=7,
+                   noisy_sd_deg=20.0, seed=5)
+    rec = Recorder([0.0], total_sweeps=40)
+    run_schedule(rec, sch)
+    sweeps = [c for c in rec.calls if c[0] == "sweep"]
+    assert len(sweeps) == 40
+    for s, c in enumerate(sweeps):
+        mode, T, sigma = sch.params(s)
+        assert (c[1], c[3], c[4]) == (mode, T, sigma)
+    runs = [c[1] for c in rec.calls if c[0] == "run"]
+    assert sum(runs) == 40 and max(runs) <= _amh.AMH_MAX_SCHED
+    # the run boundaries: mode changes (18, 20, 38, 40) and noisy restarts
+    # after sweeps 7, 14, 21, 28, 35
+    ends = list(np.cumsum(runs))
+    assert ends == [7, 14, 18, 20, 21, 28, 35, 38, 40]
+    # each noisy restart comes right after its run
+    order = [c[0] for c in rec.calls if c[0] in ("run", "noisy")]
+    assert order == ["run", "noisy", "run", "noisy", "run", "run", "run", "noisy", "run",
+                     "noisy", "run", "noisy", "run", "run"]
 
 
 def test_restart_from_best_protocol():

@@ -462,6 +462,53 @@ def test_dead_torsions_always_accepted(amh):
             assert np.all(tr["accept"][dead] == 1) and np.all(tr["dE"][dead] == 0)
 
 
+@pytest.mark.parametrize("precision,mode,kw", [
+    (32, 0, {}), (64, 0, {}), (32, 1, dict(global_kernel=1, chains_per_cta=2, threads_per_cta=128)),
+    (32, 1, dict(global_kernel=2, chains_per_cta=2, warps_per_chain=2)),
+    (64, 1, dict(chains_per_cta=2, threads_per_cta=128))])
+def test_sched_run_equals_separate_calls(amh, precision, mode, kw):
+    """amh_sweeps_sched: a run of sweeps, each at its own T and sigma, in one
+    call gives exactly what one call per sweep gives (state, trace, counts)."""
+    from paper_2211_03193_gb300._amh import AmhError, AMH_EINVAL
+    L, chains = 30, 6
+    n = 2 * L
+    prot = synth.make_protein(L, seed=350)
+    tors = synth.random_torsions(chains, L, seed=351)
+    Ts = [1.5, 0.9, 0.4, 0.2, 0.1]
+    Ss = [0.2, 0.15, 0.1, 0.07, 0.05]
+    outs = []
+    for sched in (False, True):
+        with amh.Sampler(prot, chains, tors, precision=precision, trace_chains=chains,
+                         trace_capacity=len(Ts) * n, **kw) as s:
+            if sched:
+                acc = s.sweeps_sched(mode, 8, Ts, Ss, 11)
+            else:
+                acc = sum(s.sweeps(mode, 8, T, sg, 1, 11) for T, sg in zip(Ts, Ss))
+            outs.append((acc, s.state(), [s.trace(c) for c in range(chains)]))
+            assert s.counter(0) == len(Ts) * n
+            if sched:
+                s.sweep(1, 0, 1.0, 0.1, 5, 1)  # off a sweep boundary
+                with pytest.raises(AmhError) as ei:
+                    s.sweeps_sched(mode, 8, Ts, Ss, 11)
+                assert ei.value.status == AMH_EINVAL
+    (a0, st0, tr0), (a1, st1, tr1) = outs
+    assert np.array_equal(a0, a1)
+    for x, y in zip(st0, st1):
+        assert np.array_equal(x, y)
+    for x, y in zip(tr0, tr1):
+        assert np.array_equal(x, y)
+
+
+def test_sched_run_limits(amh):
+    from paper_2211_03193_gb300._amh import AmhError
+    prot = synth.make_protein(12, seed=352)
+    with amh.Sampler(prot, 2, synth.random_torsions(2, 12, seed=353)) as s:
+        for Ts in ([1.0] * 17, [1.0, -1.0], [], [1.0, float("nan")]):
+            with pytest.raises(AmhError):
+                s.sweeps_sched(0, 8, Ts, [0.1] * len(Ts), 1)
+        assert s.counter(0) == 0
+
+
 # ---------------------------------------------------------------- local sweeps
 @pytest.mark.parametrize("precision,window", [(64, 8), (32, 8), (32, 10), (32, 5), (32, 0),
                                               (32, 3)])
