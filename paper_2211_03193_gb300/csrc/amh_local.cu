@@ -14,10 +14,12 @@
 //
 // Window coordinates come from residue transforms: with ideal geometry
 // residue i sits at T_{lo+1} o ... o T_i applied to a canonical residue in
-// the frame of residue lo, and T_i depends on (psi_{i-1}, phi_i) only.  The
-// CTA keeps every T_i of its chains in shared memory and recomputes T_p(k)
-// when move k is accepted; T_p(k) belongs to the window of move k alone
-// within a colour.
+// the frame of residue lo, and T_i depends on (psi_{i-1}, phi_i) only (in
+// FP32 from the bilinear (1, cos, sin) basis of residue_basis: two sincos
+// and 108 FMA).  The CTA keeps every T_i of its chains in shared memory and
+// recomputes T_p(k) when move k is accepted; T_p(k) belongs to the window of
+// move k alone within a colour.  Each window draws its proposal's Philox
+// words itself (they depend on the counter only).
 #include "amh_internal.h"
 
 namespace amh {
@@ -37,19 +39,53 @@ __host__ __device__ inline size_t align32l(size_t x) { return (x + 31) & ~size_t
 
 template <class R>
 struct LLayout {
-  size_t theta, draws, tr, cbs, acc, total;
+  size_t kb, theta, tr, cbs, acc, total;
   __host__ __device__ LLayout(int nmax, int Gc, int threads, int window) {
     const int h = window / 2;
     const int Lmax = nmax / 2;
     size_t o = 0;
+    kb = o;    o = align32l(o + sizeof(double) * 216);  // FP64 basis (scratch), FP32 copy after
     theta = o; o = align32l(o + sizeof(R) * (size_t)nmax * Gc);
-    draws = o; o = align32l(o + sizeof(R) * 2 * (size_t)nmax * Gc);
     tr = o;    o = align32l(o + sizeof(Pt4<R>) * 3 * (size_t)Lmax * Gc);
     cbs = o;   o = align32l(o + sizeof(R) * (size_t)(2 * h + 1) * 3 * threads);
     acc = o;   o = align32l(o + sizeof(unsigned long long) * Gc);
     total = o;
   }
 };
+
+// T_i of residue i from (psi_{i-1}, phi_i): the FP32 form takes the
+// bilinear basis of residue_basis rounded to FP32 (two sincos and 108 FMA),
+// the FP64 form NeRF in FP64.
+__device__ __forceinline__ Aff<float> local_step(const Geom<float>&, const CanonicalResidue<float>&,
+                                                 const float* kbf, float psi, float phi) {
+  float sp, cp, sf, cf;
+  sincosf(psi, &sp, &cp);
+  sincosf(phi, &sf, &cf);
+  const float f[3] = {1.f, cp, sp}, gg[3] = {1.f, cf, sf};
+  float v[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) v[q] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float w = f[a] * gg[b];
+      const float* K = kbf + (a * 3 + b) * 12;
+#pragma unroll
+      for (int q = 0; q < 12; ++q) v[q] = fmaf(w, K[q], v[q]);
+    }
+  Aff<float> T;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) T.m[q] = v[q];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) T.t[q] = v[9 + q];
+  return T;
+}
+__device__ __forceinline__ Aff<double> local_step(const Geom<double>& g,
+                                                  const CanonicalResidue<double>& cr,
+                                                  const float*, double psi, double phi) {
+  return residue_step(g, cr, psi, phi);
+}
 
 // Number of torsions k in [0, n) with k = r (mod ncol).
 __device__ __forceinline__ int colour_count(int n, int ncol, int r) {
@@ -88,8 +124,8 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ int s_group;
   const LLayout<R> lay(a.nmax, Gc, blockDim.x, a.window);
+  double* kb = (double*)(smem + lay.kb);     // residue-transform basis (FP64; FP32 copy at kb+108)
   R* th_s = (R*)(smem + lay.theta);          // [k][Gc]
-  R* dr_s = (R*)(smem + lay.draws);          // [k][Gc][2]: (z, ln u) of this sweep's proposals
   Pt4<R>* tr_s = (Pt4<R>*)(smem + lay.tr);   // [i][Gc][3]: T_i, i >= 1
   R* cbs = (R*)(smem + lay.cbs);             // [(j*3+xyz)][threads]
   unsigned long long* acc_s = (unsigned long long*)(smem + lay.acc);
@@ -97,6 +133,10 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
   const int h = a.window / 2;
   const int ncol = 4 * h > 1 ? 4 * h : 1;
   const CanonicalResidue<R> cr = canonical_residue(a.geom);
+  residue_basis(a.geom64, kb);
+  // its FP32 copy over the FP64 scratch half (kb[108..216) as 108 floats)
+  float* kbf = reinterpret_cast<float*>(kb + 108);
+  for (int q = tid; q < 108; q += nt) kbf[q] = (float)kb[q];
   for (;;) {
     __syncthreads();
     if (tid == 0) s_group = atomicAdd(a.queue, 1);
@@ -117,7 +157,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
     for (int idx = tid; idx < (L - 1) * Gc; idx += nt) {
       const int i = 1 + idx / Gc, c = idx % Gc;
       aff_store4(tr_s + ((size_t)i * Gc + c) * 3,
-                 residue_step(a.geom, cr, th_s[(2 * i - 1) * Gc + c], th_s[2 * i * Gc + c]));
+                 local_step(a.geom, cr, kbf, th_s[(2 * i - 1) * Gc + c], th_s[2 * i * Gc + c]));
     }
     const long long t0 = a.tcount[G.chain0];
     const long long nsw = a.steps_are_sweeps ? a.steps : a.steps / n;
@@ -125,18 +165,6 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
     for (long long sw = 0; sw < nsw; ++sw) {
       const R sig = a.sigma_of(sw);
       const double Tsw = a.T_of(sw);
-      // the sweep's draws, all at once (they depend on the counter only):
-      // no Philox on a window's critical path
-      for (int idx = tid; idx < n * Gc; idx += nt) {
-        const int k = idx / Gc, c = idx - k * Gc;
-        R z, lnu;
-        normal_and_lnu(draw_words(a.seed, (uint32_t)(G.chain0 + c),
-                                  (unsigned long long)(t0 + sw * n + k), 0u),
-                       &z, &lnu);
-        dr_s[2 * idx] = z;
-        dr_s[2 * idx + 1] = lnu;
-      }
-      __syncthreads();
       int slot0 = 0;  // visit slot of the colour's first torsion
       for (int r = 0; r < ncol; ++r) {
         const int cnt = colour_count(n, ncol, r);
@@ -146,7 +174,11 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
           if (c >= G.nchains) continue;
           const int k = r + w * ncol;
           const int chain = G.chain0 + c;
-          const R z = dr_s[2 * (k * Gc + c)], lnu = dr_s[2 * (k * Gc + c) + 1];
+          // the proposal's draws (they depend on the counter only)
+          R z, lnu;
+          normal_and_lnu(draw_words(a.seed, (uint32_t)chain, (unsigned long long)(t0 + sw * n + k),
+                                    0u),
+                         &z, &lnu);
           const R th = th_s[k * Gc + c];
           const R thn = propose(th, z, sig, a.lattice_K);
           const int i = k >> 1;
@@ -209,8 +241,8 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
             // orthonormality per update, ~1e-3 in later Delta-E)
             if (p >= 1 && p < L)
               aff_store4(tr_s + ((size_t)p * Gc + c) * 3,
-                         residue_step(a.geom, cr, th_s[(2 * p - 1) * Gc + c],
-                                      th_s[2 * p * Gc + c]));
+                         local_step(a.geom, cr, kbf, th_s[(2 * p - 1) * Gc + c],
+                                    th_s[2 * p * Gc + c]));
           }
           const long long v = t0 + sw * n + slot0 + w;
           if (chain < a.trace_chains && v < a.trace_cap) {
@@ -243,13 +275,18 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
   }
 }
 
-// One window's C-betas by the local kernel's builder (one thread): the
-// residue transforms as the kernel caches them (residue_step of the
-// torsions, stored and loaded through the same 4-value layout), composed
-// by window_walk.
+// One window's C-betas by the local kernel's builder: the residue
+// transforms as the kernel caches them (local_step of the torsions, stored
+// and loaded through the same 4-value layout), composed by window_walk in
+// thread 0 (the CTA's 32 threads first form the basis, as the kernel does).
 template <class R>
 __global__ void window_coords_kernel(const R* theta, int L, int k, int window, Geom<R> g,
-                                     R* out) {
+                                     Geom<double> g64, R* out) {
+  __shared__ double kb[216];
+  residue_basis(g64, kb);
+  float* kbf = reinterpret_cast<float*>(kb + 108);
+  for (int q = threadIdx.x; q < 108; q += blockDim.x) kbf[q] = (float)kb[q];
+  __syncthreads();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const CanonicalResidue<R> cr = canonical_residue(g);
   const int h = window / 2, i = k >> 1;
@@ -258,7 +295,7 @@ __global__ void window_coords_kernel(const R* theta, int L, int k, int window, G
       lo, hi,
       [&](int rr) {
         Pt4<R> q[3];
-        aff_store4(q, residue_step(g, cr, theta[2 * rr - 1], theta[2 * rr]));
+        aff_store4(q, local_step(g, cr, kbf, theta[2 * rr - 1], theta[2 * rr]));
         return aff_load4(q);
       },
       [&](int rr, const Aff<R>& M) {
@@ -274,7 +311,8 @@ __global__ void window_coords_kernel(const R* theta, int L, int k, int window, G
 template <class R>
 cudaError_t launch_window_coords(const R* theta, int L, int k, int window, Geom<R> geom, R* out,
                                  cudaStream_t st) {
-  window_coords_kernel<R><<<1, 32, 0, st>>>(theta, L, k, window, geom, out);
+  window_coords_kernel<R><<<1, 32, 0, st>>>(theta, L, k, window, geom,
+                                             ideal_geometry<double>(), out);
   return cudaGetLastError();
 }
 template cudaError_t launch_window_coords<float>(const float*, int, int, int, Geom<float>, float*,

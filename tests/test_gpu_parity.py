@@ -463,12 +463,16 @@ def test_dead_torsions_always_accepted(amh):
 
 
 @pytest.mark.parametrize("precision,mode,kw", [
-    (32, 0, {}), (64, 0, {}), (32, 1, dict(global_kernel=1, chains_per_cta=2, threads_per_cta=128)),
+    (32, 0, dict(chains_per_cta=2, threads_per_cta=128)),
+    (64, 0, dict(chains_per_cta=2, threads_per_cta=128)),
+    (32, 1, dict(global_kernel=1, chains_per_cta=2, threads_per_cta=128)),
     (32, 1, dict(global_kernel=2, chains_per_cta=2, warps_per_chain=2)),
     (64, 1, dict(chains_per_cta=2, threads_per_cta=128))])
 def test_sched_run_equals_separate_calls(amh, precision, mode, kw):
     """amh_sweeps_sched: a run of sweeps, each at its own T and sigma, in one
-    call gives exactly what one call per sweep gives (state, trace, counts)."""
+    call gives exactly what one call per sweep gives (state, trace, counts).
+    The launch shape is fixed so that both contexts sum their energies in the
+    same order."""
     from paper_2211_03193_gb300._amh import AmhError, AMH_EINVAL
     L, chains = 30, 6
     n = 2 * L
