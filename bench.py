@@ -44,12 +44,12 @@ FLOP_PER_EVAL = 16
 # DRAM bytes of one global-sweep launch from an ncu capture, per launch shape
 # (chains per CTA, threads, staging depth); valid while the kernel's sources
 # hash to sources_sha1.
-TRAFFIC_CAPTURE = {"sources_sha1": "f8ad6549657570d42f338336b41903fef0a11d73",
+TRAFFIC_CAPTURE = {"sources_sha1": "8ffa55a3693c8f49d40e531faf74fce4c87f91ac",
                    "sources": ["paper_2211_03193_gb300/csrc/amh_global.cu",
                                "paper_2211_03193_gb300/csrc/amh_device.cuh",
                                "paper_2211_03193_gb300/csrc/amh_internal.h"],
                    "workload": "amh_L300_c1024",
-                   "bytes": {(1, 1, 128, 0): 16218368}}
+                   "bytes": {(1, 1, 128, 0): 16214528}}
 
 
 def captured_traffic(workload_name, shape):
@@ -175,7 +175,7 @@ class Clocks:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -316,29 +316,45 @@ def time_to_target():
     bE = torch.empty(chains, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    reached, s = False, 0
+    reached, s, s_best = False, 0, None
+    gpu_s, med_s, s_med = None, None, None
     with torch.cuda.stream(stream):
         for s in range(total):
             mode, T, sigma = sched.params(s)
             _amh.amh_sweeps(samp.ctx, mode, w["window"], T, sigma, 1, sched.seed, None)
             if mode == _amh.AMH_GLOBAL:
                 _amh.amh_get_state(samp.ctx, None, None, bE, None)
-                if float(bE.min()) <= target:
-                    reached = True
+                now = time.perf_counter() - t0
+                if not reached and float(bE.min()) <= target:
+                    reached, gpu_s, s_best = True, now, s
+                # the median chain: a per-chain measure of the anneal's progress
+                if med_s is None and float(bE.median()) <= target:
+                    med_s, s_med = now, s
+                if reached and med_s is not None:
                     break
-    gpu_s = time.perf_counter() - t0
+    if gpu_s is None:
+        gpu_s = time.perf_counter() - t0
     final_best = float(bE.min())
+    final_median = float(bE.median())
     samp.close()
     return {"protein": "L=150, 37 bins (amh_L150_c1024 schedule, %d sweeps = 2e5 proposals "
                        "per chain)" % total,
             "target_energy": target, "cpu_runs": runs, "cpu_seconds": cpu_s,
             "cpu_proposals_per_run": total * n, "cpu_best_per_run": [float(v) for v in best],
-            "gpu_chains": chains, "gpu_seconds": gpu_s, "gpu_sweeps": s + 1,
-            "gpu_sweeps_total": total, "gpu_best_when_stopped": final_best,
+            "gpu_chains": chains, "gpu_seconds": gpu_s,
+            "gpu_sweeps": (s_best + 1) if s_best is not None else total,
+            "gpu_sweeps_total": total, "gpu_best_at_end": final_best,
             "reached": reached, "speedup": cpu_s / gpu_s if reached else None,
+            "median_chain_seconds": med_s,
+            "median_chain_sweeps": (s_med + 1) if s_med is not None else None,
+            "median_chain_best_at_end": final_median,
+            "median_chain_speedup": cpu_s / med_s if med_s else None,
             "note": "CPU: FP64 oracle, one chain per core, wall time of the 10 parallel runs; "
-                    "GPU: wall time from the first sweep until the best of its chains reaches "
-                    "the CPU runs' mean lowest energy, checked after every global sweep"}
+                    "GPU: wall time from the first sweep until the best of its chains (the "
+                    "paper's measure) and until its median chain reach the CPU runs' mean "
+                    "lowest energy, checked after every global sweep.  The best of 1024 "
+                    "chains reaches it early, in the spread of the chains at high T; the "
+                    "median chain has to anneal towards it"}
 
 
 def run_schemes():
