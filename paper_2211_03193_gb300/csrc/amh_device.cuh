@@ -765,6 +765,16 @@ __device__ __forceinline__ R wrap_angle(R a) {
   if (w > pi_<R>()) w -= tp;
   return w;
 }
+// FP32: the turn count from a product with 1/(2 pi) (one multiply, no
+// division); a count off by one at the ends is set right by the checks.
+template <>
+__device__ __forceinline__ float wrap_angle<float>(float a) {
+  const float tp = 2.f * pi_<float>();
+  float w = a - tp * floorf(fmaf(a, 0.15915494309189535f, 0.5f));
+  if (w <= -pi_<float>()) w += tp;
+  if (w > pi_<float>()) w -= tp;
+  return w;
+}
 
 // Proposed torsion for current value th, normal z and step sigma; lattice
 // mode snaps to multiples of q = 2 pi / K.

@@ -311,6 +311,24 @@ def test_teacher_forcing_follows_given_decisions(orc):
 
 
 # ---------------------------------------------------------------- RNG
+def test_synthetic_native_has_low_energy(orc):
+    """The data model behind the synthetic distograms: each pair's bin
+    probabilities peak at the hidden native trace's distance, so V of the
+    native C-betas (Eq. 5 on coordinates) lies far below V of random chain
+    starts, and below V of the native with its residues shuffled (the same
+    bond geometry, the wrong distances)."""
+    L = 80
+    prot = synth.make_protein(L, seed=1234)
+    P = orc.Problem(L, prot.p, prot.edges)
+    e_native = P.energy_cb(prot.native)
+    starts = synth.random_torsions(8, L, seed=77).astype(np.float64)
+    e_random = P.energies(starts)
+    assert e_native < 0.5 * e_random.min(), (e_native, e_random.min())
+    rng = np.random.default_rng(5)
+    e_shuffled = P.energy_cb(prot.native[rng.permutation(L)])
+    assert e_native < 0.5 * e_shuffled, (e_native, e_shuffled)
+
+
 def test_philox_known_answers(orc):
     """The oracle's Philox4x32-10 reproduces the generator's published
     known-answer vectors (tests/golden/philox4x32_10_kat.txt): a wrong
