@@ -74,6 +74,15 @@ def _init(lib, **over):
     dict(opt=dict(local_threads=512)),
     dict(opt=dict(table_texture=3)),
     dict(opt=dict(stage_table=-1)),
+    dict(opt=dict(keep_coords=2)),
+    dict(opt=dict(wait_test=-1)),
+    dict(opt=dict(global_kernel=3)),
+    dict(opt=dict(warps_per_chain=3)),
+    dict(opt=dict(global_kernel=2, precision=64)),
+    dict(opt=dict(global_kernel=2, far_pairs=1)),
+    dict(opt=dict(global_kernel=2, stage_table=1)),
+    dict(opt=dict(global_kernel=2, threads_per_cta=128)),
+    dict(opt=dict(global_kernel=2, chains_per_cta=4, warps_per_chain=4)),
 ])
 def test_bad_arguments_are_refused_before_any_device_work(lib, over):
     st, h = _init(lib, **over)
