@@ -359,15 +359,17 @@ def test_warp_kernel_limits(amh):
         s.sweep(1, 0, 1.0, 0.1, 50, 1)
 
 
-@pytest.mark.parametrize("C,wide", [(8, False), (2, False), (4, True)])
-def test_far_field_skip_equals_dense(amh, orc, C, wide):
+@pytest.mark.parametrize("C,wide,G", [(8, False, 0), (2, False, 0), (4, True, 0), (2, True, 2),
+                                      (2, False, 2)])
+def test_far_field_skip_equals_dense(amh, orc, C, wide, G):
     """FP32 global sweeps with the flat far field skipped (the default) and
     with every straddle pair evaluated, from the same states and seeds: the
     same Delta-E within FP32 rounding of the different summation order, the
     same decisions up to the first near-tie, and oracle parity (teacher-forced
     replay) for the skipping run.  L=150 from random starts: with the 37
     bins up to 20 A most (moving atom, chunk) items are far; with 64 bins up
-    to 66 A most are kept."""
+    to 66 A most are kept.  G > 0: the skipping run on the chain-group
+    kernel (G warps per chain, C chains per CTA) with its three-level filter."""
     L, chains = 150, 16
     edges = np.linspace(2.0, 66.0, 65) if wide else None
     prot = (synth.make_protein(L, edges=edges, sigma_d=2.0, seed=305) if wide
@@ -382,9 +384,11 @@ def test_far_field_skip_equals_dense(amh, orc, C, wide):
         # tolerance at this length; with 64 bins up to 66 A nearly every
         # straddle pair is inside the table's range, so the drift of the
         # moving side reaches every term and the rebuilds come twice as often
+        kw = dict(global_kernel=2, warps_per_chain=G) if (G and far == 0) else {}
         with amh.Sampler(prot, chains, tors, chains_per_cta=C, far_pairs=far,
                          resync_every=30 if wide else 60,
-                         trace_chains=chains, trace_capacity=steps) as s:
+                         trace_chains=chains, trace_capacity=steps, **kw) as s:
+            assert s.launch_config()[3] == (2 if kw else 1)
             s.sweep(1, 0, T, sigma, steps, seed)
             th_end, E_end = s.state()[:2]
             runs.append(([s.trace(c) for c in range(chains)], E_end, th_end.reshape(chains, -1)))
