@@ -263,6 +263,97 @@ __device__ __forceinline__ Aff<R> identity_map() {
   return A;
 }
 
+// ------------------------------------------------------------------ moves
+// A proposal's rigid move, y = q + M (x - p): M a rotation, p a point and
+// q its image.  Kept this way the FP32 rounding of p and q is that of one
+// stored coordinate near the moving atoms.  The affine form x -> M x + t has
+// t = p - M p rounded at the size of the coordinates (~1e-5 A at 50-80 A
+// from the origin), one shift shared by the whole moving side, and Delta-E
+// feels it with the net force on that side (~2e4 per A: up to ~0.2 for
+// one move at L=150).
+template <class R>
+struct Move {
+  R m[9];
+  R p[3];
+  R q[3];
+};
+
+// Rotation by `ang` about the line through P along the unit vector u
+// (right-handed; see rotation_axis).
+template <class R>
+__device__ __forceinline__ Move<R> move_rotation(V3<R> P, V3<R> u, R ang) {
+  const Aff<R> A = rotation_axis(P, u, ang);
+  Move<R> M;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) M.m[i] = A.m[i];
+  M.p[0] = M.q[0] = P.x;
+  M.p[1] = M.q[1] = P.y;
+  M.p[2] = M.q[2] = P.z;
+  return M;
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> move_lin(const Move<R>& A, V3<R> v) {
+  return v3<R>(fma(A.m[0], v.x, fma(A.m[1], v.y, A.m[2] * v.z)),
+               fma(A.m[3], v.x, fma(A.m[4], v.y, A.m[5] * v.z)),
+               fma(A.m[6], v.x, fma(A.m[7], v.y, A.m[8] * v.z)));
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> move_apply(const Move<R>& A, V3<R> x) {
+  const R dx = x.x - A.p[0], dy = x.y - A.p[1], dz = x.z - A.p[2];
+  return v3<R>(fma(A.m[0], dx, fma(A.m[1], dy, fma(A.m[2], dz, A.q[0]))),
+               fma(A.m[3], dx, fma(A.m[4], dy, fma(A.m[5], dz, A.q[1]))),
+               fma(A.m[6], dx, fma(A.m[7], dy, fma(A.m[8], dz, A.q[2]))));
+}
+
+// B o A (apply A first): taken about A's point, which lands on B(A(p)).
+template <class R>
+__device__ __forceinline__ Move<R> move_compose(const Move<R>& B, const Move<R>& A) {
+  Move<R> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      r.m[3 * i + j] = B.m[3 * i] * A.m[j] + B.m[3 * i + 1] * A.m[3 + j] + B.m[3 * i + 2] * A.m[6 + j];
+  const V3<R> q = move_apply(B, v3<R>(A.q[0], A.q[1], A.q[2]));
+  r.p[0] = A.p[0]; r.p[1] = A.p[1]; r.p[2] = A.p[2];
+  r.q[0] = q.x; r.q[1] = q.y; r.q[2] = q.z;
+  return r;
+}
+
+// A maps region holds A1, A2 and A21 as 12 values each at a 4-value
+// boundary (three vector loads): the rotations' M and p (their q is
+// p), and for A21 its M and q; its p is A1's (move 1's axis point).
+template <class R>
+__device__ __forceinline__ void load_rot(const R* src, Move<R>& A) {
+  const Pt4<R>* v = reinterpret_cast<const Pt4<R>*>(src);
+  const Pt4<R> a = v[0], b = v[1], d = v[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.p[0] = A.q[0] = d.y; A.p[1] = A.q[1] = d.z; A.p[2] = A.q[2] = d.w;
+}
+
+// A21 from its 12 values and A1's point p1.
+template <class R>
+__device__ __forceinline__ void load_move21(const R* src, const R* p1, Move<R>& A) {
+  const Pt4<R>* v = reinterpret_cast<const Pt4<R>*>(src);
+  const Pt4<R> a = v[0], b = v[1], d = v[2];
+  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
+  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
+  A.m[8] = d.x; A.q[0] = d.y; A.q[1] = d.z; A.q[2] = d.w;
+  A.p[0] = p1[0]; A.p[1] = p1[1]; A.p[2] = p1[2];
+}
+
+// The 12 values of a rotation (pt = p) or of A21 (pt = q).
+template <class R>
+__device__ __forceinline__ void store_move(R* dst, const Move<R>& A, const R* pt) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dst[i] = A.m[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) dst[9 + i] = pt[i];
+}
+
 // ------------------------------------------------------------------ parallel G(s)
 // Every residue is the same rigid body (ideal geometry), so G(s) is a chain
 // of rigid transforms: with residue 0 in the canonical frame of

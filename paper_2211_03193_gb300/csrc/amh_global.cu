@@ -261,96 +261,6 @@ __device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P)
   full_energy(s, a.tab, P.tab_off, P.L);
 }
 
-// A proposal's rigid move, y = q + M (x - p): M a rotation, p a point and
-// q its image.  Kept this way the FP32 rounding of p and q is that of one
-// stored coordinate near the moving atoms.  The affine form x -> M x + t has
-// t = p - M p rounded at the size of the coordinates (~1e-5 A at 50-80 A
-// from the origin), one shift shared by the whole moving side, and Delta-E
-// feels it with the net force on that side (~2e4 per A: up to ~0.2 for
-// one move at L=150).
-template <class R>
-struct Move {
-  R m[9];
-  R p[3];
-  R q[3];
-};
-
-// Rotation by `ang` about the line through P along the unit vector u
-// (right-handed; see rotation_axis).
-template <class R>
-__device__ __forceinline__ Move<R> move_rotation(V3<R> P, V3<R> u, R ang) {
-  const Aff<R> A = rotation_axis(P, u, ang);
-  Move<R> M;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) M.m[i] = A.m[i];
-  M.p[0] = M.q[0] = P.x;
-  M.p[1] = M.q[1] = P.y;
-  M.p[2] = M.q[2] = P.z;
-  return M;
-}
-
-template <class R>
-__device__ __forceinline__ V3<R> move_lin(const Move<R>& A, V3<R> v) {
-  return v3<R>(fma(A.m[0], v.x, fma(A.m[1], v.y, A.m[2] * v.z)),
-               fma(A.m[3], v.x, fma(A.m[4], v.y, A.m[5] * v.z)),
-               fma(A.m[6], v.x, fma(A.m[7], v.y, A.m[8] * v.z)));
-}
-
-template <class R>
-__device__ __forceinline__ V3<R> move_apply(const Move<R>& A, V3<R> x) {
-  const R dx = x.x - A.p[0], dy = x.y - A.p[1], dz = x.z - A.p[2];
-  return v3<R>(fma(A.m[0], dx, fma(A.m[1], dy, fma(A.m[2], dz, A.q[0]))),
-               fma(A.m[3], dx, fma(A.m[4], dy, fma(A.m[5], dz, A.q[1]))),
-               fma(A.m[6], dx, fma(A.m[7], dy, fma(A.m[8], dz, A.q[2]))));
-}
-
-// B o A (apply A first): taken about A's point, which lands on B(A(p)).
-template <class R>
-__device__ __forceinline__ Move<R> move_compose(const Move<R>& B, const Move<R>& A) {
-  Move<R> r;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      r.m[3 * i + j] = B.m[3 * i] * A.m[j] + B.m[3 * i + 1] * A.m[3 + j] + B.m[3 * i + 2] * A.m[6 + j];
-  const V3<R> q = move_apply(B, v3<R>(A.q[0], A.q[1], A.q[2]));
-  r.p[0] = A.p[0]; r.p[1] = A.p[1]; r.p[2] = A.p[2];
-  r.q[0] = q.x; r.q[1] = q.y; r.q[2] = q.z;
-  return r;
-}
-
-// The maps region holds per chain A1, A2 and A21 as 12 values each at a
-// 4-value boundary (three vector loads): the rotations' M and p (their q is
-// p), and for A21 its M and q; its p is A1's (move 1's axis point).
-template <class R, int C>
-__device__ __forceinline__ void load_rot(const R* src, Move<R>& A) {
-  const Pt4<R>* v = reinterpret_cast<const Pt4<R>*>(src);
-  const Pt4<R> a = v[0], b = v[1], d = v[2];
-  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
-  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
-  A.m[8] = d.x; A.p[0] = A.q[0] = d.y; A.p[1] = A.q[1] = d.z; A.p[2] = A.q[2] = d.w;
-}
-
-// A21 from its 12 values and A1's point p1.
-template <class R, int C>
-__device__ __forceinline__ void load_move21(const R* src, const R* p1, Move<R>& A) {
-  const Pt4<R>* v = reinterpret_cast<const Pt4<R>*>(src);
-  const Pt4<R> a = v[0], b = v[1], d = v[2];
-  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
-  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
-  A.m[8] = d.x; A.q[0] = d.y; A.q[1] = d.z; A.q[2] = d.w;
-  A.p[0] = p1[0]; A.p[1] = p1[1]; A.p[2] = p1[2];
-}
-
-// The 12 values of a rotation (pt = p) or of A21 (pt = q).
-template <class R>
-__device__ __forceinline__ void store_move(R* dst, const Move<R>& A, const R* pt) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) dst[i] = A.m[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) dst[9 + i] = pt[i];
-}
-
 // Straddle-block Delta-E (moving side [m0, m1), fixed side [f0, f1)).
 // Items are (moving atom, chunk of kFC fixed atoms); with LIST the items
 // run are the nlist entries of `list` (item indices mi * nch + ch).
@@ -374,13 +284,13 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     // the maps are read per item (only the moved positions stay live in the
     // pair loop, leaving registers for more loads in flight)
     Move<R> A;
-    load_rot<R, C>(s.maps + 36 * c, A);
+    load_rot(s.maps + 36 * c, A);
     const V3<R> y1 = move_apply(A, xm);
     V3<R> y2, y21;
     if (FUSED) {
-      load_move21<R, C>(s.maps + 36 * c + 24, A.p, A);
+      load_move21(s.maps + 36 * c + 24, A.p, A);
       y21 = move_apply(A, xm);
-      load_rot<R, C>(s.maps + 36 * c + 12, A);
+      load_rot(s.maps + 36 * c + 12, A);
       y2 = move_apply(A, xm);
     }
     const int fb = f0 + ch * kFC, fe = min(fb + kFC, f1);
@@ -502,14 +412,14 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
     if ((real >> c) & 1u) {
       const V3<float> xm = s.cb(m0 + mi, c);
       Move<float> A;
-      load_rot<float, C>(s.maps + 36 * c, A);
+      load_rot(s.maps + 36 * c, A);
       const V3<float> y1 = move_apply(A, xm);
       V3<float> o;
       float r2;
       if (FUSED) {
-        load_move21<float, C>(s.maps + 36 * c + 24, A.p, A);
+        load_move21(s.maps + 36 * c + 24, A.p, A);
         const V3<float> y21 = move_apply(A, xm);
-        load_rot<float, C>(s.maps + 36 * c + 12, A);
+        load_rot(s.maps + 36 * c + 12, A);
         const V3<float> y2 = move_apply(A, xm);
         o = (xm + y1 + y2 + y21) * 0.25f;
         r2 = fmaxf(fmaxf(dist2(xm, o), dist2(y1, o)), fmaxf(dist2(y2, o), dist2(y21, o)));
@@ -614,10 +524,10 @@ __device__ bool pair_block_staged(Shm<float, C>& s, const Tab<float>& tb, long l
   const int RB = Bp * (int)sizeof(float2);
   const float2* tab = tb.E + tab_off;
   Move<float> A1, A2, A21;
-  load_rot<float, C>(s.maps + 36 * c, A1);
+  load_rot(s.maps + 36 * c, A1);
   if (FUSED) {
-    load_rot<float, C>(s.maps + 36 * c + 12, A2);
-    load_move21<float, C>(s.maps + 36 * c + 24, A1.p, A21);
+    load_rot(s.maps + 36 * c + 12, A2);
+    load_move21(s.maps + 36 * c + 24, A1.p, A21);
   }
   const int nF = f1 - f0;
   const int nch = (nF + kFC - 1) / kFC;
@@ -733,9 +643,9 @@ __device__ void commit_moves(Shm<R, C>& s, int m0, int m1, bool cb_only) {
   if (!code) return;
   Move<R> A;
   if (code < 3)
-    load_rot<R, C>(s.maps + 36 * c + 12 * (code - 1), A);
+    load_rot(s.maps + 36 * c + 12 * (code - 1), A);
   else
-    load_move21<R, C>(s.maps + 36 * c + 24, s.maps + 36 * c + 9, A);
+    load_move21(s.maps + 36 * c + 24, s.maps + 36 * c + 9, A);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int rest = idx / C;
     const int v = cb_only ? 3 : rest & 3, i = m0 + (cb_only ? rest : rest >> 2);

@@ -143,71 +143,6 @@ struct Grp {
   }
 };
 
-// --- moves (the same arithmetic as the CTA kernel's: y = q + M (x - p)) ---
-struct WMove {
-  float m[9];
-  float p[3];
-  float q[3];
-};
-
-__device__ __forceinline__ WMove wmove_rotation(V3<float> P, V3<float> u, float ang) {
-  const Aff<float> A = rotation_axis(P, u, ang);
-  WMove M;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) M.m[i] = A.m[i];
-  M.p[0] = M.q[0] = P.x;
-  M.p[1] = M.q[1] = P.y;
-  M.p[2] = M.q[2] = P.z;
-  return M;
-}
-__device__ __forceinline__ V3<float> wmove_lin(const WMove& A, V3<float> v) {
-  return v3<float>(fmaf(A.m[0], v.x, fmaf(A.m[1], v.y, A.m[2] * v.z)),
-                   fmaf(A.m[3], v.x, fmaf(A.m[4], v.y, A.m[5] * v.z)),
-                   fmaf(A.m[6], v.x, fmaf(A.m[7], v.y, A.m[8] * v.z)));
-}
-__device__ __forceinline__ V3<float> wmove_apply(const WMove& A, V3<float> x) {
-  const float dx = x.x - A.p[0], dy = x.y - A.p[1], dz = x.z - A.p[2];
-  return v3<float>(fmaf(A.m[0], dx, fmaf(A.m[1], dy, fmaf(A.m[2], dz, A.q[0]))),
-                   fmaf(A.m[3], dx, fmaf(A.m[4], dy, fmaf(A.m[5], dz, A.q[1]))),
-                   fmaf(A.m[6], dx, fmaf(A.m[7], dy, fmaf(A.m[8], dz, A.q[2]))));
-}
-// B o A, about A's point
-__device__ __forceinline__ WMove wmove_compose(const WMove& B, const WMove& A) {
-  WMove r;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      r.m[3 * i + j] = B.m[3 * i] * A.m[j] + B.m[3 * i + 1] * A.m[3 + j] + B.m[3 * i + 2] * A.m[6 + j];
-  const V3<float> q = wmove_apply(B, v3<float>(A.q[0], A.q[1], A.q[2]));
-  r.p[0] = A.p[0]; r.p[1] = A.p[1]; r.p[2] = A.p[2];
-  r.q[0] = q.x; r.q[1] = q.y; r.q[2] = q.z;
-  return r;
-}
-// 12 stored values: M and a point (p for a rotation, whose q is p; q for A21,
-// whose p is A1's)
-__device__ __forceinline__ void wstore(float* dst, const WMove& A, const float* pt) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) dst[i] = A.m[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) dst[9 + i] = pt[i];
-}
-__device__ __forceinline__ void wload_rot(const float* src, WMove& A) {
-  const Pt4<float>* v = reinterpret_cast<const Pt4<float>*>(src);
-  const Pt4<float> a = v[0], b = v[1], d = v[2];
-  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
-  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
-  A.m[8] = d.x; A.p[0] = A.q[0] = d.y; A.p[1] = A.q[1] = d.z; A.p[2] = A.q[2] = d.w;
-}
-__device__ __forceinline__ void wload_21(const float* src, const float* p1, WMove& A) {
-  const Pt4<float>* v = reinterpret_cast<const Pt4<float>*>(src);
-  const Pt4<float> a = v[0], b = v[1], d = v[2];
-  A.m[0] = a.x; A.m[1] = a.y; A.m[2] = a.z; A.m[3] = a.w;
-  A.m[4] = b.x; A.m[5] = b.y; A.m[6] = b.z; A.m[7] = b.w;
-  A.m[8] = d.x; A.q[0] = d.y; A.q[1] = d.z; A.q[2] = d.w;
-  A.p[0] = p1[0]; A.p[1] = p1[1]; A.p[2] = p1[2];
-}
-
 __device__ __forceinline__ float wdist2(V3<float> a, V3<float> b) {
   const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -277,27 +212,27 @@ __device__ void wspheres(WShm& w, const Grp& g, int L, int f0, int f1) {
 // coordinates and under the moves, added to the Delta-E sums.
 template <bool FUSED, bool TEX>
 __device__ __forceinline__ void wpair(const WShm& w, const Tab<float>& tb, long long tab_off, int L,
-                                      int m, int f, const WMove& A1, const WMove& A2,
-                                      const WMove& A21, float& acc1, float& acc2, float& acc21) {
+                                      int m, int f, const Move<float>& A1, const Move<float>& A2,
+                                      const Move<float>& A21, float& acc1, float& acc2, float& acc21) {
   const V3<float> xm = w.x(m), xf = w.x(f);
   const int r = m < f ? row_of(L, m, f) : row_of(L, f, m);
-  const V3<float> y1 = wmove_apply(A1, xm);
+  const V3<float> y1 = move_apply(A1, xm);
   float e0, e1, e2 = 0.f, e21 = 0.f;
   if constexpr (TEX) {
     const int rowe = (int)tab_off + r * tb.Bp;
     e0 = pair_term_tex(rowe, dist_fast(xf, xm), tb);
     e1 = pair_term_tex(rowe, dist_fast(xf, y1), tb);
     if (FUSED) {
-      e2 = pair_term_tex(rowe, dist_fast(xf, wmove_apply(A2, xm)), tb);
-      e21 = pair_term_tex(rowe, dist_fast(xf, wmove_apply(A21, xm)), tb);
+      e2 = pair_term_tex(rowe, dist_fast(xf, move_apply(A2, xm)), tb);
+      e21 = pair_term_tex(rowe, dist_fast(xf, move_apply(A21, xm)), tb);
     }
   } else {
     const float2* row = tb.E + tab_off + (long long)r * tb.Bp;
     e0 = pair_term(row, dist_fast(xf, xm), tb);
     e1 = pair_term(row, dist_fast(xf, y1), tb);
     if (FUSED) {
-      e2 = pair_term(row, dist_fast(xf, wmove_apply(A2, xm)), tb);
-      e21 = pair_term(row, dist_fast(xf, wmove_apply(A21, xm)), tb);
+      e2 = pair_term(row, dist_fast(xf, move_apply(A2, xm)), tb);
+      e21 = pair_term(row, dist_fast(xf, move_apply(A21, xm)), tb);
     }
   }
   acc1 += e1 - e0;
@@ -325,23 +260,23 @@ __device__ void wblock(WShm& w, const Grp& grp, const Tab<float>& tb, long long 
                        int m0, int m1, int f0, int f1, float cut, float& s1, float& s2,
                        float& s21, unsigned long long& count) {
   const int lane = grp.lane;
-  WMove A1, A2, A21;
-  wload_rot(w.maps, A1);
+  Move<float> A1, A2, A21;
+  load_rot(w.maps, A1);
   A2 = A1;
   A21 = A1;
   if (FUSED) {
-    wload_rot(w.maps + 12, A2);
-    wload_21(w.maps + 24, A1.p, A21);
+    load_rot(w.maps + 12, A2);
+    load_move21(w.maps + 24, A1.p, A21);
   }
   const int nM = m1 - m0;
   // (1) image spheres of the moving atoms
   for (int mi = grp.t; mi < nM; mi += grp.nt) {
     const V3<float> xm = w.x(m0 + mi);
-    const V3<float> y1 = wmove_apply(A1, xm);
+    const V3<float> y1 = move_apply(A1, xm);
     V3<float> o;
     float r2;
     if (FUSED) {
-      const V3<float> y2 = wmove_apply(A2, xm), y21 = wmove_apply(A21, xm);
+      const V3<float> y2 = move_apply(A2, xm), y21 = move_apply(A21, xm);
       o = (xm + y1 + y2 + y21) * 0.25f;
       r2 = fmaxf(fmaxf(wdist2(xm, o), wdist2(y1, o)), fmaxf(wdist2(y2, o), wdist2(y21, o)));
     } else {
@@ -589,18 +524,18 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
         // k1 odd: psi_i about CA_i -> C_i; k1 even: phi_i about N_i -> CA_i
         const int i = k1 >> 1;
         const float d = wrap_angle(thn - th);
-        const WMove A = wmove_rotation(w.axis(i, 0), w.axis(i, (k1 & 1) ? 2 : 1), up ? -d : d);
+        const Move<float> A = move_rotation(w.axis(i, 0), w.axis(i, (k1 & 1) ? 2 : 1), up ? -d : d);
         if (t < 2) {
-          wstore(w.maps + 12 * t, A, A.p);
+          store_move(w.maps + 12 * t, A, A.p);
         } else {
           const float z2 = w.draws[2 * (j + 1 - d0)];
           const float th2 = w.theta[k + 1];
           const float d2 = wrap_angle(propose(th2, z2, sig, a.lattice_K) - th2);
           const V3<float> P2 = w.axis(p, 0), u2 = w.axis(p, 1);  // phi_p: N_p -> CA_p
-          const V3<float> P2m = up ? P2 : wmove_apply(A, P2);
-          const V3<float> u2m = up ? u2 : wmove_lin(A, u2);
-          const WMove A21 = wmove_compose(wmove_rotation(P2m, u2m, up ? -d2 : d2), A);
-          wstore(w.maps + 24, A21, A21.q);
+          const V3<float> P2m = up ? P2 : move_apply(A, P2);
+          const V3<float> u2m = up ? u2 : move_lin(A, u2);
+          const Move<float> A21 = move_compose(move_rotation(P2m, u2m, up ? -d2 : d2), A);
+          store_move(w.maps + 24, A21, A21.q);
         }
       }
     }
@@ -675,21 +610,21 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
       // commit: the moving side turns by the accepted map; an upstream move
       // turns only C-betas (the rest of this sweep rotates about bonds at or
       // after the pivot, and a new sweep starts from a rebuild)
-      WMove A;
+      Move<float> A;
       if (code < 3)
-        wload_rot(w.maps + 12 * (code - 1), A);
+        load_rot(w.maps + 12 * (code - 1), A);
       else
-        wload_21(w.maps + 24, w.maps + 9, A);
+        load_move21(w.maps + 24, w.maps + 9, A);
       const int per = up ? 1 : 4;
       const int total = (m1 - m0) * per;
       for (int idx = t; idx < total; idx += nt) {
         const int v = up ? 3 : (idx & 3), i = m0 + (up ? idx : idx >> 2);
         if (v == 0)
-          w.set_axis(i, 0, wmove_apply(A, w.axis(i, 0)));
+          w.set_axis(i, 0, move_apply(A, w.axis(i, 0)));
         else if (v < 3)
-          w.set_axis(i, v, wmove_lin(A, w.axis(i, v)));
+          w.set_axis(i, v, move_lin(A, w.axis(i, v)));
         else
-          w.set_x(i, wmove_apply(A, w.x(i)));
+          w.set_x(i, move_apply(A, w.x(i)));
       }
       // the chunks' unmoved ranges lose [m0, m1)
       if (up) {
