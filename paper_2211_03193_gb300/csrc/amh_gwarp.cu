@@ -37,7 +37,6 @@ constexpr size_t kKbBytes = 1792;  // residue-transform basis: 216 doubles, 128-
 
 __host__ __device__ inline size_t wal(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Shared memory of one warp (one chain of up to Lmax residues).
 constexpr int kBatch = 32;  // pairs evaluated at a time: one per lane
 constexpr int kPairCap = 32 * kWC + kBatch;  // one round of 32 items of kWC pairs plus a partial batch
 constexpr int kMaxG = 4;                     // warps per chain at most
