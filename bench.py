@@ -38,6 +38,10 @@ FP32_LANES_PER_SM = 128
 # coordinate), 1 sub (fraction), 1 sub + 1 mul + 1 add (interpolation),
 # 1 add (accumulate) = 16
 FLOP_PER_EVAL = 16
+# a term whose distance is formed and found flat (at or past the last bin
+# centre in every configuration of its pair, so its entry is not read):
+# the squared distance (8), the square root (1) and the bin coordinate (2)
+FLOP_PER_FLAT = 11
 # DRAM bytes (read + write) of one launch of the global-sweep kernel, from one
 # ncu capture (profiles/global_kernel_L300_c1024.md).  Reported only while
 # the kernel's sources and launch shape are the ones that were captured.
@@ -744,7 +748,7 @@ def run_ours(args):
     step_ms = []
     glob_ev = []
     launches[0] = 0
-    terms0 = samp.pair_terms()  # straddle-pair terms evaluated so far (synchronises)
+    terms0 = samp.pair_terms()  # straddle terms (read, formed) so far (synchronises)
     with Clocks(local, args.clocks_csv or None) as clk:
         for _ in range(args.steps):
             with torch.cuda.stream(stream):
@@ -758,7 +762,11 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     timed_launches = launches[0]
-    terms_glob = (samp.pair_terms() - terms0) / args.steps  # per global sweep, this rank
+    terms1 = samp.pair_terms()
+    # per global sweep, this rank: terms read and interpolated; terms whose
+    # distance was formed and found flat
+    terms_glob = (terms1[0] - terms0[0]) / args.steps
+    flat_glob = ((terms1[1] - terms0[1]) - (terms1[0] - terms0[0])) / args.steps
     total_ms = sum(a.elapsed_time(b_) for a, b_ in step_ms)
     glob_ms = [a.elapsed_time(b_) for a, b_ in glob_ev]
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -811,13 +819,14 @@ def run_ours(args):
     pk, src = peaks()
     clocks = clk.summary()
     g_ms = float(np.mean(glob_ms)) if glob_ms else float("nan")
-    # terms per global launch: the straddle blocks' (all of them with
-    # --far-pairs 1, else those not skipped as flat; counted by the library)
-    # plus the full energy each call ends with
+    # terms per global launch: the straddle blocks' terms read (counted by
+    # the library: pairs skipped as flat, by chunk or by pair, are not) plus
+    # the full energy each call ends with; the flat pairs' formed distances
+    # are counted apart at their own cost
     dense = 2 * (L ** 3 - L) // 3 * chains
     resync_terms = (L * (L - 1) // 2) * chains
     evals_glob_launch = int(terms_glob) + resync_terms
-    achieved = evals_glob_launch * FLOP_PER_EVAL / (g_ms / 1000.0) / 1e12
+    achieved = (evals_glob_launch * FLOP_PER_EVAL + flat_glob * FLOP_PER_FLAT) / (g_ms / 1000.0) / 1e12
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     peak_tf = sm_count * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     fetch = (", table rows staged %d deep" % D if D else
@@ -835,6 +844,7 @@ def run_ours(args):
             "kernel": kname,
             "launch_ms": g_ms, "pair_evals_per_launch": evals_glob_launch,
             "straddle_terms_dense": dense, "straddle_terms_evaluated": int(terms_glob),
+            "straddle_terms_flat_tested": int(flat_glob), "flop_per_flat_term": FLOP_PER_FLAT,
             # the rate the same launch time would mean if every straddle pair
             # were evaluated (the skipped ones add exactly zero): a speed
             # figure, not arithmetic the kernel performs

@@ -291,14 +291,21 @@ amh_status amh_get_trace(amh_ctx* ctx, int chain, amh_trace_rec* out, long long*
 amh_status amh_counter(amh_ctx* ctx, int chain, long long* t);
 
 /*
- * amh_pair_terms -- straddle-pair terms the global sweeps of this context
- * have evaluated so far (Sec. 2.4 scores every pair of the block a < p(k) <=
- * b; each term is e(|x_a - x_b|) at one configuration: the current one or a
- * proposal's).  With far_pairs = 0 the terms of pairs that stay beyond the
- * last bin centre are skipped and not counted.  *evaluated (host) is
- * cumulative since amh_init; synchronises the context's stream.
+ * amh_pair_terms -- straddle-pair terms of the global sweeps of this context
+ * so far (Sec. 2.4 scores every pair of the block a < p(k) <= b; each term is
+ * e(|x_a - x_b|) at one configuration: the current one or a proposal's).
+ *   *evaluated: terms whose table entry was read and interpolated;
+ *   *formed (may be NULL): terms whose distance was formed, i.e. the
+ *   evaluated ones plus, in the FP32 form, those of pairs found to lie at or
+ *   past the last bin centre in every configuration (flat: they add exactly
+ *   zero, so their entries are not read).
+ * With far_pairs = 0 the pairs that whole chunk tests place beyond the last
+ * bin centre are skipped before any distance is formed and counted in
+ * neither.  Host pointers; cumulative since amh_init; synchronises the
+ * context's stream.  AMH_EINVAL if evaluated is NULL.
  */
-amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated);
+amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated,
+                          unsigned long long* formed);
 
 /*
  * amh_philox -- the sampler's random stream, for checking: for

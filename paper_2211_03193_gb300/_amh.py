@@ -77,7 +77,8 @@ def load() -> ctypes.CDLL:
     L.amh_noisy_restart.argtypes = [vp, ctypes.c_double, ctypes.c_ulonglong]
     L.amh_get_trace.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_longlong)]
     L.amh_counter.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
-    L.amh_pair_terms.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.amh_pair_terms.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong),
+                                 ctypes.POINTER(ctypes.c_ulonglong)]
     L.amh_philox.argtypes = [ctypes.c_ulonglong, ctypes.c_uint, ctypes.c_ulonglong, ctypes.c_uint,
                              ctypes.c_longlong, vp, vp, vp]
     L.amh_last_error.argtypes = [vp]
@@ -224,11 +225,13 @@ def amh_counter(ctx, chain) -> int:
     return t.value
 
 
-def amh_pair_terms(ctx) -> int:
-    """Straddle-pair terms evaluated by the context's global sweeps so far."""
+def amh_pair_terms(ctx):
+    """(evaluated, formed): straddle-pair terms of the context's global sweeps
+    so far whose table entries were read, and whose distances were formed."""
     v = ctypes.c_ulonglong()
-    _check(load().amh_pair_terms(ctx, ctypes.byref(v)), ctx)
-    return v.value
+    f = ctypes.c_ulonglong()
+    _check(load().amh_pair_terms(ctx, ctypes.byref(v), ctypes.byref(f)), ctx)
+    return v.value, f.value
 
 
 def amh_philox(seed, chain, t0, stream, count):

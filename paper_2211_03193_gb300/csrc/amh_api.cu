@@ -46,7 +46,7 @@ struct amh_ctx {
   int nlgroups[6] = {0, 0, 0, 0, 0, 0};
   int* queue = nullptr;
   int* err = nullptr;
-  unsigned long long* pair_count = nullptr;  // straddle-pair terms evaluated by global sweeps
+  unsigned long long* pair_count = nullptr;  // global sweeps' straddle terms: [0] formed, [1] read
   TraceRec* trace = nullptr;
   long long* trace_count = nullptr;
   // launch configuration
@@ -900,8 +900,8 @@ amh_status amh_init(amh_ctx** out, int n_proteins, const int* L, const int* chai
   CKI(cudaMalloc(&ctx->queue, sizeof(int)));
   CKI(cudaMalloc(&ctx->err, sizeof(int)));
   CKI(cudaMemset(ctx->err, 0, sizeof(int)));
-  CKI(cudaMalloc(&ctx->pair_count, sizeof(unsigned long long)));
-  CKI(cudaMemset(ctx->pair_count, 0, sizeof(unsigned long long)));
+  CKI(cudaMalloc(&ctx->pair_count, 2 * sizeof(unsigned long long)));
+  CKI(cudaMemset(ctx->pair_count, 0, 2 * sizeof(unsigned long long)));
   if (o.keep_coords) {
     // 3 values per residue per chain: half the torsion count times 3
     const size_t rs = o.precision == 64 ? sizeof(double) : sizeof(float);
@@ -1195,13 +1195,16 @@ amh_status amh_counter(amh_ctx* ctx, int chain, long long* t) {
   return AMH_OK;
 }
 
-amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated) {
+amh_status amh_pair_terms(amh_ctx* ctx, unsigned long long* evaluated,
+                          unsigned long long* formed) {
   amh_status st = check_ctx(ctx);
   if (st) return st;
   if (!evaluated) return set_err(ctx, AMH_EINVAL, "evaluated is NULL");
-  CK(ctx, cudaMemcpyAsync(evaluated, ctx->pair_count, sizeof(unsigned long long),
-                          cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned long long v[2];
+  CK(ctx, cudaMemcpyAsync(v, ctx->pair_count, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  *evaluated = v[1];
+  if (formed) *formed = v[0];
   return AMH_OK;
 }
 

@@ -723,6 +723,45 @@ __device__ __forceinline__ float pair_term_tex(int row_e, float d, const Tab<flo
   return fmaf(us, v.y, v.x);
 }
 
+// The FP32 term split in two, so that a pair can be tested before its entry
+// is read.  bin_sat: the saturated bin coordinate us of a distance; us == 1
+// exactly when d is at or past the last bin centre, where every distance of
+// the row reads the same flat entry (and the same term, bit for bit).
+__device__ __forceinline__ float bin_sat(float d, const Tab<float>& tb) {
+  return __saturatef(fmaf(d, tb.k1, tb.k2));
+}
+
+// The term at bin coordinate us, its entry fetched through the texture path
+// only where `need` is nonzero; elsewhere nothing is read and the result is
+// 0.  The fetch is predicated rather than branched around, so a warp whose
+// lanes disagree keeps its loads in flight together and the texture unit
+// only serves the lanes that read.
+__device__ __forceinline__ float term_tex_if(int row_e, float us, const Tab<float>& tb,
+                                             unsigned need) {
+  const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
+  const int e = row_e - 0x4B000000 + __float_as_int(f);
+  float x = 0.f, y = 0.f, z = 0.f, w = 0.f;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+      "@q tex.1d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%6}];\n\t}"
+      : "+f"(x), "+f"(y), "+f"(z), "+f"(w)
+      : "l"((unsigned long long)tb.tex), "r"(need), "r"(e));
+  return fmaf(us, y, x);
+}
+
+// The same through L1 loads from the row's address.
+__device__ __forceinline__ float term_ldg_if(const float2* __restrict__ row, float us,
+                                             const Tab<float>& tb, unsigned need) {
+  const float f = __fmaf_rd(us, tb.umax, 8388608.0f);
+  const char* base = reinterpret_cast<const char*>(row) - 8ull * 0x4B000000u;
+  float x = 0.f, y = 0.f;
+  asm("{\n\t.reg .pred q;\n\t.reg .u64 ad;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+      "mad.wide.u32 ad, %2, 8, %4;\n\t"
+      "@q ld.global.nc.v2.f32 {%0, %1}, [ad];\n\t}"
+      : "+f"(x), "+f"(y)
+      : "r"((unsigned)__float_as_int(f)), "r"(need), "l"(base));
+  return fmaf(us, y, x);
+}
+
 // The same term read from a row staged in shared memory (32-bit address:
 // one multiply-add forms the entry address).
 __device__ __forceinline__ float pair_term_smem(uint32_t row, float d, const Tab<float>& tb) {

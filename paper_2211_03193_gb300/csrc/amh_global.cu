@@ -163,9 +163,12 @@ __device__ __forceinline__ V3<R> to_r(V3<double> v) {
 // (~1e-4 A at L=300).  The torsion axes are kept as CA and two unit bond
 // directions formed in FP64: a direction from two FP32 atoms 1.46 A apart
 // would be off by up to ulp(|x|) / 1.46 A (2.6e-6 rad at 50 A), and a move
-// would carry its whole side off by that angle times the move's angle.
+// would carry its whole side off by that angle times the move's angle.  Not
+// inlined: the FP64 scan needs far more registers than the proposal loop,
+// and as a call of its own it no longer sets the whole kernel's allocation
+// (it runs once per sweep; its spills stay inside it).
 template <class R, int C>
-__device__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
+__device__ __noinline__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
   build_chains_scan(
       g, s.kb, L, C, [&](int c, int k) { return (double)s.theta[k * C + c]; },
       [&](int c, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
@@ -263,11 +266,14 @@ __device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P)
 
 // Straddle-block Delta-E (moving side [m0, m1), fixed side [f0, f1)).
 // Items are (moving atom, chunk of kFC fixed atoms); with LIST the items
-// run are the nlist entries of `list` (item indices mi * nch + ch).
+// run are the nlist entries of `list` (item indices mi * nch + ch).  FP32:
+// a pair whose images all lie at or past the last bin centre adds exactly
+// zero (each reads the row's one flat entry), so its entries are not read;
+// nread counts the pairs that were read, for the chain slots set in `real`.
 template <class R, int C, bool FUSED, bool TEX, bool LIST = false>
 __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, int L, int m0,
-                           int m1, int f0, int f1, const unsigned short* list = nullptr,
-                           int nlist = 0) {
+                           int m1, int f0, int f1, unsigned real, unsigned& nread,
+                           const unsigned short* list = nullptr, int nlist = 0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   constexpr int S = 32 / C;
   const int c = lane % C, sl = lane / C;
@@ -275,6 +281,7 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
   const int nF = f1 - f0;
   const int nch = (nF + kFC - 1) / kFC;
   const int items = LIST ? nlist : (m1 - m0) * nch;
+  const unsigned live = (real >> c) & 1u;
   typename AccT<R>::T acc1 = 0, acc2 = 0, acc21 = 0;
   for (int q = gs; q < items; q += G) {
     const int it = LIST ? (int)list[q] : q;
@@ -306,14 +313,34 @@ __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, in
     for (int f = fb; f < fe; ++f) {
       const V3<R> xf = s.cb(f, c);
       R e0, e1, e2 = 0, e21 = 0;
-      if constexpr (TEX) {
-        e0 = pair_term_tex(rowe, dist_fast(xf, xm), tb);
-        e1 = pair_term_tex(rowe, dist_fast(xf, y1), tb);
+      if constexpr (sizeof(R) == 4) {
+        const float u0 = bin_sat(dist_fast(xf, xm), tb), u1 = bin_sat(dist_fast(xf, y1), tb);
+        float u2 = 1.f, u21 = 1.f;
         if (FUSED) {
-          e2 = pair_term_tex(rowe, dist_fast(xf, y2), tb);
-          e21 = pair_term_tex(rowe, dist_fast(xf, y21), tb);
+          u2 = bin_sat(dist_fast(xf, y2), tb);
+          u21 = bin_sat(dist_fast(xf, y21), tb);
         }
-        rowe += step * tb.Bp;
+        // read nothing when every image is flat: the terms are then 0 - 0
+        // instead of the flat value minus itself, the same exact zero
+        const unsigned need = fminf(fminf(u0, u1), fminf(u2, u21)) < 1.f;
+        nread += (need & live) << (FUSED ? 2 : 1);  // terms read
+        if constexpr (TEX) {
+          e0 = term_tex_if(rowe, u0, tb, need);
+          e1 = term_tex_if(rowe, u1, tb, need);
+          if (FUSED) {
+            e2 = term_tex_if(rowe, u2, tb, need);
+            e21 = term_tex_if(rowe, u21, tb, need);
+          }
+          rowe += step * tb.Bp;
+        } else {
+          e0 = term_ldg_if(row, u0, tb, need);
+          e1 = term_ldg_if(row, u1, tb, need);
+          if (FUSED) {
+            e2 = term_ldg_if(row, u2, tb, need);
+            e21 = term_ldg_if(row, u21, tb, need);
+          }
+          row += (long long)step * tb.Bp;
+        }
       } else {
         e0 = pair_term(row, dist_fast(xf, xm), tb);
         e1 = pair_term(row, dist_fast(xf, y1), tb);
@@ -392,7 +419,7 @@ __device__ void far_spheres(Shm<float, C>& s, int f0, int f1, int t0, int nt) {
 template <int C, bool FUSED, bool TEX>
 __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long tab_off, int L,
                                int m0, int m1, int f0, int f1, float cut, unsigned real,
-                               unsigned long long& count) {
+                               unsigned long long& count, unsigned& nread) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const int nM = m1 - m0, nJ = (f1 - f0 + kFC - 1) / kFC;
   const int nMs = s.nm;  // stride of s.bits per chain
@@ -474,7 +501,8 @@ __device__ void pair_block_far(Shm<float, C>& s, const Tab<float>& tb, long long
   }
   __syncthreads();
   // (4) the kept items through the full block's pair loop
-  pair_block<float, C, FUSED, TEX, true>(s, tb, tab_off, L, m0, m1, f0, f1, s.list, total);
+  pair_block<float, C, FUSED, TEX, true>(s, tb, tab_off, L, m0, m1, f0, f1, real, nread, s.list,
+                                         total);
 }
 
 // The straddle block with its table rows staged in shared memory.  Each warp
@@ -746,6 +774,16 @@ __device__ void store_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev&
   }
 }
 
+// Add the table terms read by a warp's lanes since the last flush to the
+// context's counter (called by every thread of the CTA).
+__device__ __forceinline__ void flush_reads(unsigned& nread, unsigned long long* dst) {
+  unsigned v = nread;
+  nread = 0;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0 && v && dst) atomicAdd(dst, (unsigned long long)v);
+}
+
 template <class R, int C, bool ST>
 __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G,
                           const ProteinDev& P, unsigned& par, int* abort_flag) {
@@ -758,7 +796,8 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   rebuild(s, a, P);
   long long since = 0;
   const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
-  unsigned long long count = 0;  // straddle-pair terms evaluated (lane 0 of each warp)
+  unsigned long long count = 0;  // straddle-pair distances formed (thread 0)
+  unsigned nread = 0;            // FP32 terms whose entries this thread read
   long long d0 = 0, dend = 0;  // proposals [d0, dend) have their draws in s.draws
   int kn = (int)(t0 % n);      // torsion index of proposal t0 + j (kept without a 64-bit modulo)
   long long sw = 0;            // sweep of the call (scheduled calls start on a sweep boundary)
@@ -769,6 +808,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       // the Philox draws of the next kDraw proposals, by all threads (they
       // depend on the counter only): the serial step keeps the rotations
       __syncthreads();
+      if (a.pair_count) flush_reads(nread, a.pair_count + 1);
       d0 = j;
       dend = j + kDraw;
       for (int idx = threadIdx.x; idx < kDraw * C; idx += blockDim.x) {
@@ -910,34 +950,34 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
         if (a.tab.tex) {
           if (fused)
             pair_block_far<C, true, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
-                                          count);
+                                          count, nread);
           else
             pair_block_far<C, false, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
-                                           count);
+                                           count, nread);
         } else {
           if (fused)
             pair_block_far<C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
-                                           count);
+                                           count, nread);
           else
             pair_block_far<C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, real,
-                                            count);
+                                            count, nread);
         }
       } else if (a.tab.tex) {
         if (fused)
-          pair_block<R, C, true, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+          pair_block<R, C, true, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, real, nread);
         else
-          pair_block<R, C, false, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+          pair_block<R, C, false, true>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, real, nread);
       } else {
         if (fused)
-          pair_block<R, C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+          pair_block<R, C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, real, nread);
         else
-          pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+          pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, real, nread);
       }
     } else {
       if (fused)
-        pair_block<R, C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+        pair_block<R, C, true, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, real, nread);
       else
-        pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1);
+        pair_block<R, C, false, false>(s, a.tab, P.tab_off, L, m0, m1, f0, f1, real, nread);
     }
     if (threadIdx.x == 0 && !(sizeof(R) == 4 && !ST && a.far_skip))
       count += (unsigned long long)(m1 - m0) * (f1 - f0) * min(G.nchains, C) * (fused ? 4 : 2);
@@ -968,16 +1008,19 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
           d21 += pp[2];
         }
       }
-      const double Tc = chain_T(a, P, chain, Tsw);
-      // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE (no division)
-      const int acc1 = (double)s.lnu[c] * Tc < -d1;
+      // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE (no division),
+      // in the form's precision (FP32: the product's rounding, 6e-8
+      // relative, is far inside the 1e-5 tie margin of the decisions; the
+      // FP64 pipe runs at 1/64 of the FP32 rate here)
+      const R Tr = (R)chain_T(a, P, chain, Tsw);
+      const int acc1 = s.lnu[c] * Tr < -(R)d1;
       int code = acc1;
       if (acc1) s.theta[k * C + c] = s.thn[c];
       put_trace(a, c < G.nchains, chain, t, k, acc1, s.thn[c], s.lnu[c], d1);
       int acc2 = 0;
       if (fused) {
         const double e2 = acc1 ? d21 : d2;
-        acc2 = (double)s.lnu[C + c] * Tc < -e2;
+        acc2 = s.lnu[C + c] * Tr < -(R)e2;
         if (acc2) {
           code = acc1 ? 3 : 2;
           s.theta[(k + 1) * C + c] = s.thn[C + c];
@@ -1006,7 +1049,15 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   }
   store_coords(s, a, G, P);
   store_group(s, a, G, P, t0 + steps, true);
-  if (a.pair_count && count) atomicAdd(a.pair_count, count);
+  if (a.pair_count) {
+    // FP64 and staged sweeps read every term they form
+    if (sizeof(R) == 8 || ST) nread = 0;
+    flush_reads(nread, a.pair_count + 1);
+    if (count) {
+      atomicAdd(a.pair_count, count);
+      if (sizeof(R) == 8 || ST) atomicAdd(a.pair_count + 1, count);
+    }
+  }
 }
 
 template <class R, int C, bool ST>

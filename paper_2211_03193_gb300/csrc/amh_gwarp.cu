@@ -681,7 +681,10 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
   unsigned long long c = count;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-  if (q.lane == 0 && a.pair_count && c) atomicAdd(a.pair_count, c);
+  if (q.lane == 0 && a.pair_count && c) {  // every pair it forms is read
+    atomicAdd(a.pair_count, c);
+    atomicAdd(a.pair_count + 1, c);
+  }
   q.sync();
 }
 

@@ -76,7 +76,7 @@ struct SweepArgs {
   int window;           // local sweeps: d
   int stage_depth;      // global sweeps, staged variant: ring slots per warp
   int far_skip;         // FP32 global sweeps: skip chunks whose pairs stay flat
-  unsigned long long* pair_count;  // straddle-pair terms evaluated (global sweeps), or null
+  unsigned long long* pair_count;  // global sweeps' straddle terms [formed, read], or null
   float far_cut;        // distance beyond which an FP32 term is exactly flat, plus a margin
   const double* ladder; // per-slot temperature factors (parallel tempering) or null
   int ladder_K;         // ladder size: chain c of protein p runs at T * ladder[(c - chain0) % K]

@@ -154,8 +154,9 @@ class Sampler:
         with, built from the chain's current torsions in residue lo's frame."""
         return _amh.amh_window_coords(self.ctx, chain, k, window)
 
-    def pair_terms(self) -> int:
-        """Straddle-pair terms the global sweeps have evaluated so far."""
+    def pair_terms(self):
+        """(evaluated, formed) straddle-pair terms of the global sweeps so far:
+        entries read, and distances formed (see amh_pair_terms)."""
         return _amh.amh_pair_terms(self.ctx)
 
     def close(self):

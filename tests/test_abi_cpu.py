@@ -95,7 +95,7 @@ def test_null_context_calls_return_estate(lib):
     assert lib.amh_energy(None, None) == 5
     assert lib.amh_sweep(None, 1, 0, 1.0, 0.1, 10, 1, None) == 5
     v = ctypes.c_ulonglong()
-    assert lib.amh_pair_terms(None, ctypes.byref(v)) == 5
+    assert lib.amh_pair_terms(None, ctypes.byref(v), None) == 5
     lib.amh_destroy(None)
 
 
