@@ -465,7 +465,9 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
   const long long steps = a.steps_are_sweeps ? a.steps * n : a.steps;
   const double lad = a.ladder ? a.ladder[(chain - P.chain0) % a.ladder_K] : 1.0;
   long long sw = 0;  // sweep of the call (scheduled calls start on a sweep boundary)
-  double Tc = a.T_of(0) * lad;
+  // decisions in FP32, the form's precision (the product's rounding is far
+  // inside the 1e-5 tie margin; the FP64 pipe runs at 1/64 of the FP32 rate)
+  float Tf = (float)(a.T_of(0) * lad);
   float sig = a.sigma_of(0);
   const bool traced = chain < a.trace_chains;
   // decisions need Delta-E only and the exit recomputes V from scratch, so
@@ -493,7 +495,7 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
     const int k = kn;
     if (k == 0 && j > 0 && a.nsched) {
       ++sw;
-      Tc = a.T_of(sw) * lad;
+      Tf = (float)(a.T_of(sw) * lad);
       sig = a.sigma_of(sw);
     }
     if (since >= a.resync_every || (k == 0 && j > 0)) {
@@ -542,7 +544,7 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
     if (dead) {
       // phi_0 and psi_{L-1} move no C-beta: Delta-E = 0, always accepted
       const float thn = w.maps[36], lnu = w.maps[38];
-      const int acc = (double)lnu * Tc < -0.0;
+      const int acc = lnu * Tf < -0.f;
       if (t == 0) {
         if (acc) w.theta[k] = thn;
         if (traced && tp < a.trace_cap) {
@@ -570,14 +572,13 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
       wblock<false, TEX>(w, q, a.tab, P.tab_off, L, m0, m1, f0, f1, a.far_cut, s1, s2, s21,
                          count);
     // Eq. 1 with T > 0: ln u < -dE / T  <=>  T ln u < -dE, taken by every thread
-    const double d1 = s1, d2 = s2, d21 = s21;
     const float thn1 = w.maps[36], lnu1 = w.maps[38];
-    const int acc1 = (double)lnu1 * Tc < -d1;
+    const int acc1 = lnu1 * Tf < -s1;
     int code = acc1, acc2 = 0;
-    double e2 = 0.0;
+    float e2 = 0.f;
     if (fused) {
-      e2 = acc1 ? d21 : d2;
-      acc2 = (double)w.maps[39] * Tc < -e2;
+      e2 = acc1 ? s21 : s2;
+      acc2 = w.maps[39] * Tf < -e2;
       if (acc2) code = acc1 ? 3 : 2;
     }
     if (t == 0) {
@@ -588,7 +589,7 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
         r.accept = acc1;
         r.theta_new = (double)thn1;
         r.lnu = (double)lnu1;
-        r.dE = d1;
+        r.dE = (double)s1;
         a.trace[(size_t)chain * a.trace_cap + tp] = r;
       }
       if (fused) {
@@ -599,7 +600,7 @@ __device__ void wrun_chain(WShm& w, const Grp& q, const SweepArgs<float>& a, con
           r.accept = acc2;
           r.theta_new = (double)w.maps[37];
           r.lnu = (double)w.maps[39];
-          r.dE = e2;
+          r.dE = (double)e2;
           a.trace[(size_t)chain * a.trace_cap + tp + 1] = r;
         }
       }

@@ -138,9 +138,9 @@ def replay_and_compare(orc, prot, s0, tr, mode, window, T, sigma, t0, seed, chai
                            tol[bad][:5] if np.ndim(tol) else tol, exact[bad][:5],
                            npairs[bad][:5] if np.ndim(npairs) else npairs)
     # every GPU decision follows Eq. 1 from the GPU's own ln u and Delta-E,
-    # in the precision the kernel decides in (FP32 local sweeps: FP32; the
-    # rest: FP64 products of the stored values)
-    if not fp64 and mode == orc.LOCAL:
+    # in the precision the kernel decides in (the FP32 form: FP32 products;
+    # the FP64 form: FP64)
+    if not fp64:
         own = (tr["lnu"].astype(np.float32) * np.float32(T)) < -tr["dE"].astype(np.float32)
     else:
         own = tr["lnu"] * T < -tr["dE"]
