@@ -172,13 +172,12 @@ __device__ __forceinline__ V3<R> apply(const Aff<R>& A, V3<R> x) {
                fma(A.m[6], x.x, fma(A.m[7], x.y, fma(A.m[8], x.z, A.t[2]))));
 }
 
-// Right-handed rotation by angle `ang` about the line through P along the
-// unit vector u.  Raising a dihedral by delta turns the far-side atoms by
+// Right-handed rotation about the line through P along the unit vector u,
+// by the angle whose sine and cosine are s and c (rotation_axis: by the
+// angle itself).  Raising a dihedral by delta turns the far-side atoms by
 // +delta about the bond from its second to its third atom.
 template <class R>
-__device__ __forceinline__ Aff<R> rotation_axis(V3<R> P, V3<R> u, R ang) {
-  R s, c;
-  sincos_(ang, &s, &c);
+__device__ __forceinline__ Aff<R> rotation_axis_cs(V3<R> P, V3<R> u, R s, R c) {
   R oc = R(1) - c;
   Aff<R> A;
   A.m[0] = c + u.x * u.x * oc;
@@ -195,6 +194,12 @@ __device__ __forceinline__ Aff<R> rotation_axis(V3<R> P, V3<R> u, R ang) {
   A.t[1] = P.y - (A.m[3] * P.x + A.m[4] * P.y + A.m[5] * P.z);
   A.t[2] = P.z - (A.m[6] * P.x + A.m[7] * P.y + A.m[8] * P.z);
   return A;
+}
+template <class R>
+__device__ __forceinline__ Aff<R> rotation_axis(V3<R> P, V3<R> u, R ang) {
+  R s, c;
+  sincos_(ang, &s, &c);
+  return rotation_axis_cs(P, u, s, c);
 }
 
 // The same about the axis through P towards Q.
@@ -278,11 +283,11 @@ struct Move {
   R q[3];
 };
 
-// Rotation by `ang` about the line through P along the unit vector u
-// (right-handed; see rotation_axis).
+// Rotation about the line through P along the unit vector u (right-handed;
+// see rotation_axis_cs), by the angle of sine s and cosine c, or by `ang`.
 template <class R>
-__device__ __forceinline__ Move<R> move_rotation(V3<R> P, V3<R> u, R ang) {
-  const Aff<R> A = rotation_axis(P, u, ang);
+__device__ __forceinline__ Move<R> move_rotation_cs(V3<R> P, V3<R> u, R s, R c) {
+  const Aff<R> A = rotation_axis_cs(P, u, s, c);
   Move<R> M;
 #pragma unroll
   for (int i = 0; i < 9; ++i) M.m[i] = A.m[i];
@@ -290,6 +295,12 @@ __device__ __forceinline__ Move<R> move_rotation(V3<R> P, V3<R> u, R ang) {
   M.p[1] = M.q[1] = P.y;
   M.p[2] = M.q[2] = P.z;
   return M;
+}
+template <class R>
+__device__ __forceinline__ Move<R> move_rotation(V3<R> P, V3<R> u, R ang) {
+  R s, c;
+  sincos_(ang, &s, &c);
+  return move_rotation_cs(P, u, s, c);
 }
 
 template <class R>

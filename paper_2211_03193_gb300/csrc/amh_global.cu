@@ -21,7 +21,7 @@ namespace amh {
 namespace {
 
 constexpr int kFC = kPairChunk;  // fixed-side atoms per work item
-constexpr int kDraw = 64;          // proposals whose draws are made ahead, all at once
+constexpr int kDraw = 64;          // proposals made ahead, all at once
 
 template <class R>
 struct AccT {
@@ -57,7 +57,7 @@ struct Layout {
     bb = o;    o = align16(o + sizeof(R) * (size_t)Lmax * 9 * C);
     ls = Lmax | 1;
     cb = o;    o = align16(o + sizeof(Pt4<R>) * (size_t)ls * C);
-    draws = o; o = align16(o + sizeof(R) * 2 * kDraw * C);
+    draws = o; o = align16(o + sizeof(R) * 4 * kDraw * C);
     kb = o;    o = align16(o + sizeof(double) * 216);
     maps = o;  o = align16(o + sizeof(R) * 36 * C);
     list = o;  o = align16(o + (far ? sizeof(unsigned short) * (size_t)nM * nJ : 0));
@@ -84,7 +84,7 @@ struct Shm {
   R* theta;  // [k][C]
   R* bb;     // [((i*3+v)*3+xyz)][C]: v 0 CA_i, 1 unit N_i -> CA_i, 2 unit CA_i -> C_i
   Pt4<R>* cb4;  // [C][ls]: chain-major, odd stride
-  R* draws;     // [kDraw][C][2]: (z, ln u) of the next proposals
+  R* draws;     // [kDraw][C][4]: (theta', ln u, sin, cos of the rotation) of the next proposals
   double* kb;   // residue-transform basis (residue_basis), 216 doubles
   R* maps;   // [C][36]: moves A1, A2, A21 (see load_rot)
   unsigned short* list;  // items kept by the far-field test, in order
@@ -804,33 +804,48 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   double Tsw = a.T_of(0);
   R sig = a.sigma_of(0);
   for (long long j = 0; j < steps;) {
-    if (j + 2 > dend) {
-      // the Philox draws of the next kDraw proposals, by all threads (they
-      // depend on the counter only): the serial step keeps the rotations
-      __syncthreads();
-      if (a.pair_count) flush_reads(nread, a.pair_count + 1);
-      d0 = j;
-      dend = j + kDraw;
-      for (int idx = threadIdx.x; idx < kDraw * C; idx += blockDim.x) {
-        const int q = idx / C, c = idx - q * C;
-        R z, lnu;
-        normal_and_lnu(draw_words(a.seed, (uint32_t)(G.chain0 + c),
-                                  (unsigned long long)(t0 + j + q), 0u),
-                       &z, &lnu);
-        s.draws[2 * idx] = z;
-        s.draws[2 * idx + 1] = lnu;
-      }
-      __syncthreads();
-    }
     const long long t = t0 + j;
     const int k = kn;
-    // periodic rebuild, and one at each new sweep inside a call (commits of
-    // upstream moves leave torsion axes behind, see commit_moves)
     if (k == 0 && j > 0 && a.nsched) {
       ++sw;
       Tsw = a.T_of(sw);
       sig = a.sigma_of(sw);
     }
+    if (j + 2 > dend) {
+      // the next proposals of this sweep (up to kDraw), made ahead by all
+      // threads: their Philox draws depend on the counter only, and the
+      // torsion each one changes is touched by no other proposal of the
+      // sweep, so its value is final now.  The proposed value and the sine
+      // and cosine of the rotation (signed for the side that moves) are
+      // stored; the serial step keeps only the maps.
+      __syncthreads();
+      if (a.pair_count) flush_reads(nread, a.pair_count + 1);
+      d0 = j;
+      const int nb = min(kDraw, n - k);
+      dend = j + nb;
+      for (int idx = threadIdx.x; idx < nb * C; idx += blockDim.x) {
+        const int q = idx / C, c = idx - q * C;
+        const int kq = k + q;
+        R z, lnu;
+        normal_and_lnu(draw_words(a.seed, (uint32_t)(G.chain0 + c),
+                                  (unsigned long long)(t0 + j + q), 0u),
+                       &z, &lnu);
+        const R th = s.theta[kq * C + c];
+        const R thn = propose(th, z, sig, a.lattice_K);
+        const R d = wrap_angle(thn - th);
+        const int pq = (kq + 1) >> 1;
+        R sn, cs;
+        sincos_(pq <= L - pq ? -d : d, &sn, &cs);
+        R* dr = s.draws + 4 * idx;
+        dr[0] = thn;
+        dr[1] = lnu;
+        dr[2] = sn;
+        dr[3] = cs;
+      }
+      __syncthreads();
+    }
+    // periodic rebuild, and one at each new sweep inside a call (commits of
+    // upstream moves leave torsion axes behind, see commit_moves)
     if (since >= a.resync_every || (k == 0 && j > 0)) {
       rebuild(s, a, P);
       since = 0;
@@ -856,31 +871,25 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       const int q = threadIdx.x;
       if (q == 0 || (q < 3 && fused)) {
         const int k1 = q == 1 ? k + 1 : k;
-        const R z = s.draws[2 * (j + (k1 - k) - d0)];
-        const R lnu = s.draws[2 * (j + (k1 - k) - d0) + 1];
-        const R th = s.theta[k1];
-        const R thn = propose(th, z, sig, a.lattice_K);
+        const R* dr = s.draws + 4 * (j + (k1 - k) - d0);
         if (q < 2) {
-          s.thn[q] = thn;
-          s.lnu[q] = lnu;
+          s.thn[q] = dr[0];
+          s.lnu[q] = dr[1];
         }
         if (!dead) {
           // k1 odd: psi_i about CA_i -> C_i; k1 even: phi_i about N_i -> CA_i
           const int i = k1 >> 1;
-          const R d = wrap_angle(thn - th);
           const Move<R> A =
-              move_rotation(s.bbv(i, 0, 0), s.bbv(i, (k1 & 1) ? 2 : 1, 0), up ? -d : d);
+              move_rotation_cs(s.bbv(i, 0, 0), s.bbv(i, (k1 & 1) ? 2 : 1, 0), dr[2], dr[3]);
           if (q < 2) {
             store_move(s.maps + 12 * q, A, A.p);
           } else {
-            const R z2 = s.draws[2 * (j + 1 - d0)];
-            const R th2 = s.theta[k + 1];
-            const R d2 = wrap_angle(propose(th2, z2, sig, a.lattice_K) - th2);
+            const R* dr2 = s.draws + 4 * (j + 1 - d0);
             const V3<R> P2 = s.bbv(p, 0, 0), u2 = s.bbv(p, 1, 0);  // phi_p: N_p -> CA_p
             // after move 1 the axis of move 2 has moved with the far side
             const V3<R> P2m = up ? P2 : move_apply(A, P2);
             const V3<R> u2m = up ? u2 : move_lin(A, u2);
-            const Move<R> A21 = move_compose(move_rotation(P2m, u2m, up ? -d2 : d2), A);
+            const Move<R> A21 = move_compose(move_rotation_cs(P2m, u2m, dr2[2], dr2[3]), A);
             store_move(s.maps + 24, A21, A21.q);
           }
         }
@@ -888,33 +897,26 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     } else {
       if (threadIdx.x < C) {
         const int c = threadIdx.x;
-        const R z = s.draws[2 * ((j - d0) * C + c)], lnu = s.draws[2 * ((j - d0) * C + c) + 1];
-        const R th = s.theta[k * C + c];
-        const R thn = propose(th, z, sig, a.lattice_K);
-        s.thn[c] = thn;
-        s.lnu[c] = lnu;
+        const R* dr = s.draws + 4 * ((j - d0) * C + c);
+        s.thn[c] = dr[0];
+        s.lnu[c] = dr[1];
         if (!dead) {
-          const R d1 = wrap_angle(thn - th);
           // k odd: psi_i about CA_i -> C_i; k even: phi_i about N_i -> CA_i
           const int i = k >> 1;
           const Move<R> A1 =
-              move_rotation(s.bbv(i, 0, c), s.bbv(i, (k & 1) ? 2 : 1, c), up ? -d1 : d1);
+              move_rotation_cs(s.bbv(i, 0, c), s.bbv(i, (k & 1) ? 2 : 1, c), dr[2], dr[3]);
           store_move(s.maps + 36 * c, A1, A1.p);
           if (fused) {
-            const R z2 = s.draws[2 * ((j + 1 - d0) * C + c)];
-            const R lnu2 = s.draws[2 * ((j + 1 - d0) * C + c) + 1];
-            const R th2 = s.theta[(k + 1) * C + c];
-            const R thn2 = propose(th2, z2, sig, a.lattice_K);
-            s.thn[C + c] = thn2;
-            s.lnu[C + c] = lnu2;
-            const R d2 = wrap_angle(thn2 - th2);
+            const R* dr2 = s.draws + 4 * ((j + 1 - d0) * C + c);
+            s.thn[C + c] = dr2[0];
+            s.lnu[C + c] = dr2[1];
             const V3<R> P2 = s.bbv(p, 0, c), u2 = s.bbv(p, 1, c);  // phi_p: N_p -> CA_p
-            const Move<R> A2 = move_rotation(P2, u2, up ? -d2 : d2);
+            const Move<R> A2 = move_rotation_cs(P2, u2, dr2[2], dr2[3]);
             store_move(s.maps + 36 * c + 12, A2, A2.p);
             // after move 1 the axis of move 2 has moved with the far side
             const V3<R> P2m = up ? P2 : move_apply(A1, P2);
             const V3<R> u2m = up ? u2 : move_lin(A1, u2);
-            const Move<R> A2m = move_rotation(P2m, u2m, up ? -d2 : d2);
+            const Move<R> A2m = move_rotation_cs(P2m, u2m, dr2[2], dr2[3]);
             const Move<R> A21 = move_compose(A2m, A1);
             store_move(s.maps + 36 * c + 24, A21, A21.q);
           }
@@ -927,7 +929,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       if (threadIdx.x < C) {
         const int c = threadIdx.x;
         const int chain = G.chain0 + c;
-        const int acc = (double)s.lnu[c] * chain_T(a, P, chain, Tsw) < -0.0;
+        const int acc = s.lnu[c] * (R)chain_T(a, P, chain, Tsw) < -R(0);
         if (acc) s.theta[k * C + c] = s.thn[c];
         s.acc[c] += acc;
         put_trace(a, c < G.nchains, chain, t, k, acc, s.thn[c], s.lnu[c], 0.0);
