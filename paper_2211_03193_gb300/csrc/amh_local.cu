@@ -107,6 +107,40 @@ __device__ __forceinline__ double local_term<double>(const Tab<double>& tb, long
   return pair_term(tb.E + tab_off + (long long)row * tb.Bp, d, tb);
 }
 
+// Delta V_local of a window's pairs on the texture path (FP32): for each
+// downstream atom b, the upstream atoms a in [lo, p) up to kLA at a time with
+// no branch, so a thread keeps 2 kLA fetches in flight (a loop over a waits
+// for each pair's fetches in turn).  Slots past p, and pairs at or past the
+// last bin centre both before and after the move, read nothing and add
+// 0 - 0; the terms are added in the order of the plain loop below, so the
+// sum is the same bit for bit.  cbs: the window's C-betas, [(j*3+xyz)][nt].
+constexpr int kLA = 8;  // windows up to d = 14 (p - lo <= h + 1)
+
+__device__ __forceinline__ float window_pairs_tex(const float* cbs, int nt, int tid, int L,
+                                                  int lo, int p, int hi, const Aff<float>& A,
+                                                  const Tab<float>& tb, long long tab_off) {
+  const int na = p - lo;
+  float acc = 0.f;
+  for (int b = p; b <= hi; ++b) {
+    const int jb = b - lo;
+    const V3<float> xb = v3<float>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
+                                   cbs[(jb * 3 + 2) * nt + tid]);
+    const V3<float> yb = apply(A, xb);
+#pragma unroll
+    for (int q = 0; q < kLA; ++q) {
+      const unsigned ok = q < na;
+      const int jq = ok ? q : 0;
+      const V3<float> xa = v3<float>(cbs[(jq * 3 + 0) * nt + tid], cbs[(jq * 3 + 1) * nt + tid],
+                                     cbs[(jq * 3 + 2) * nt + tid]);
+      const int re = (int)tab_off + row_of(L, lo + jq, b) * tb.Bp;
+      const float u1 = bin_sat(dist_fast(xa, yb), tb), u0 = bin_sat(dist_fast(xa, xb), tb);
+      const unsigned need = ok & (fminf(u0, u1) < 1.f);
+      acc += term_tex_if(re, u1, tb, need) - term_tex_if(re, u0, tb, need);
+    }
+  }
+  return acc;
+}
+
 // The window builder: residue rr of [lo, hi] sits at M_rr = T_{lo+1} o ...
 // o T_rr applied to the canonical residue (the frame of residue lo); Ti(rr)
 // gives T_rr and emit(rr, M_rr) receives each residue's map in order.
@@ -210,7 +244,14 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                   }
                 });
             A = rotation(Pax, Qax, wrap_angle(thn - th));
-            for (int b = p; b <= hi; ++b) {
+            bool done = false;
+            if constexpr (sizeof(R) == 4) {
+              if (a.tab.tex && p - lo <= kLA) {
+                acc = window_pairs_tex(cbs, nt, tid, L, lo, p, hi, A, a.tab, P.tab_off);
+                done = true;
+              }
+            }
+            for (int b = p; b <= hi && !done; ++b) {
               const int jb = b - lo;
               const V3<R> xb = v3<R>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
                                      cbs[(jb * 3 + 2) * nt + tid]);
