@@ -359,6 +359,38 @@ def test_warp_kernel_limits(amh):
         s.sweep(1, 0, 1.0, 0.1, 50, 1)
 
 
+def test_pair_term_counters(amh):
+    """amh_pair_terms over one global sweep from a sweep boundary: with every
+    pair formed (far_pairs = 1) the distances formed are the straddle terms
+    of Sec. 2.4 exactly, 4 per pair of each fused proposal pair, sum over p of
+    p (L - p) = (L^3 - L) / 6 pairs, so 2 (L^3 - L) / 3 per chain; the FP32
+    form reads the entries of fewer (pairs whose images all lie at or past the
+    last bin centre are only tested), the FP64 form of all.  The chunk tests
+    (far_pairs = 0) form fewer distances but drop only flat pairs, so the
+    terms read are the same whenever the two runs take the same decisions."""
+    L, chains = 60, 8
+    prot = synth.make_protein(L, seed=371)
+    tors = synth.random_torsions(chains, L, seed=372)
+    n = 2 * L
+    dense = 2 * (L ** 3 - L) // 3 * chains
+    got = {}
+    for prec, far in ((32, 1), (32, 0), (64, 1)):
+        with amh.Sampler(prot, chains, tors, precision=prec, far_pairs=far, chains_per_cta=1,
+                         threads_per_cta=128) as s:
+            e0, f0 = s.pair_terms()
+            s.sweep(1, 0, 0.8, 8 * DEG, n, 12)
+            e1, f1 = s.pair_terms()
+            got[prec, far] = (e1 - e0, f1 - f0, s.torsions())
+    ev, fo, th1 = got[32, 1]
+    assert fo == dense
+    assert 0 < ev < fo
+    ev0, fo0, th0 = got[32, 0]
+    assert ev0 <= fo0 < dense
+    if np.array_equal(th0, th1):
+        assert ev0 == ev
+    assert got[64, 1][:2] == (dense, dense)
+
+
 @pytest.mark.parametrize("C,wide,G", [(8, False, 0), (2, False, 0), (4, True, 0), (2, True, 2),
                                       (2, False, 2)])
 def test_far_field_skip_equals_dense(amh, orc, C, wide, G):
