@@ -187,6 +187,12 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
       th_s[k * Gc + c] = v;
     }
     if (tid < Gc) acc_s[tid] = 0ull;
+    // accepted moves counted per thread and added once per call: when the
+    // block size is a multiple of Gc every item of a thread belongs to chain
+    // slot tid % Gc (one shared atomic per acceptance serialised the
+    // accepting windows of a chain)
+    const bool own_slot = nt % Gc == 0;
+    unsigned nacc = 0;
     __syncthreads();
     for (int idx = tid; idx < (L - 1) * Gc; idx += nt) {
       const int i = 1 + idx / Gc, c = idx % Gc;
@@ -276,7 +282,10 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                                             : (double)lnu * Tc < -dE;
           if (accept) {
             th_s[k * Gc + c] = thn;
-            atomicAdd(&acc_s[c], 1ull);
+            if (own_slot)
+              ++nacc;
+            else
+              atomicAdd(&acc_s[c], 1ull);
             // T_p depends on torsions 2p-1 and 2p, one of which is k: rebuilt
             // from them (composing the move into T_p instead lost ~1e-6 of
             // orthonormality per update, ~1e-3 in later Delta-E)
@@ -300,6 +309,8 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
         __syncthreads();
       }
     }
+    if (own_slot && nacc) atomicAdd(&acc_s[tid % Gc], (unsigned long long)nacc);
+    __syncthreads();
     const long long t_end = t0 + nsw * n;
     for (int idx = tid; idx < n * Gc; idx += nt) {
       const int c = idx / n, k = idx - c * n;
