@@ -802,6 +802,9 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   int kn = (int)(t0 % n);      // torsion index of proposal t0 + j (kept without a 64-bit modulo)
   long long sw = 0;            // sweep of the call (scheduled calls start on a sweep boundary)
   double Tsw = a.T_of(0);
+  // the temperature of this thread's chain slot in the form's precision
+  // (threads below C take the decisions), formed once per sweep
+  R Tc = (R)chain_T(a, P, G.chain0 + (int)(threadIdx.x % C), Tsw);
   R sig = a.sigma_of(0);
   for (long long j = 0; j < steps;) {
     const long long t = t0 + j;
@@ -809,6 +812,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
     if (k == 0 && j > 0 && a.nsched) {
       ++sw;
       Tsw = a.T_of(sw);
+      Tc = (R)chain_T(a, P, G.chain0 + (int)(threadIdx.x % C), Tsw);
       sig = a.sigma_of(sw);
     }
     if (j + 2 > dend) {
@@ -929,7 +933,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       if (threadIdx.x < C) {
         const int c = threadIdx.x;
         const int chain = G.chain0 + c;
-        const int acc = s.lnu[c] * (R)chain_T(a, P, chain, Tsw) < -R(0);
+        const int acc = s.lnu[c] * Tc < -R(0);
         if (acc) s.theta[k * C + c] = s.thn[c];
         s.acc[c] += acc;
         put_trace(a, c < G.nchains, chain, t, k, acc, s.thn[c], s.lnu[c], 0.0);
@@ -989,21 +993,16 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       const int c = threadIdx.x;
       const int chain = G.chain0 + c;
       const int W = blockDim.x >> 5;
-      double d1, d2, d21;
-      if constexpr (sizeof(R) == 4) {  // FP32 partials, summed over the warps in FP32
-        float f1 = 0.f, f2 = 0.f, f21 = 0.f;
-        for (int w = 0; w < W; ++w) {
+      // the partial sums over the warps: FP32 in the FP32 form (each partial
+      // is an FP32 sum already), FP64 in the FP64 form
+      typename AccT<R>::T d1 = 0, d2 = 0, d21 = 0;
+      for (int w = 0; w < W; ++w) {
+        if constexpr (sizeof(R) == 4) {
           const float* pp = s.partf + (size_t)(w * C + c) * 3;
-          f1 += pp[0];
-          f2 += pp[1];
-          f21 += pp[2];
-        }
-        d1 = f1;
-        d2 = f2;
-        d21 = f21;
-      } else {
-        d1 = d2 = d21 = 0.0;
-        for (int w = 0; w < W; ++w) {
+          d1 += pp[0];
+          d2 += pp[1];
+          d21 += pp[2];
+        } else {
           const double* pp = s.part + (size_t)(w * C + c) * 3;
           d1 += pp[0];
           d2 += pp[1];
@@ -1014,20 +1013,20 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
       // in the form's precision (FP32: the product's rounding, 6e-8
       // relative, is far inside the 1e-5 tie margin of the decisions; the
       // FP64 pipe runs at 1/64 of the FP32 rate here)
-      const R Tr = (R)chain_T(a, P, chain, Tsw);
-      const int acc1 = s.lnu[c] * Tr < -(R)d1;
+      const int acc1 = s.lnu[c] * Tc < -d1;
       int code = acc1;
       if (acc1) s.theta[k * C + c] = s.thn[c];
-      put_trace(a, c < G.nchains, chain, t, k, acc1, s.thn[c], s.lnu[c], d1);
+      put_trace(a, c < G.nchains, chain, t, k, acc1, s.thn[c], s.lnu[c], (double)d1);
       int acc2 = 0;
       if (fused) {
-        const double e2 = acc1 ? d21 : d2;
-        acc2 = s.lnu[C + c] * Tr < -(R)e2;
+        const typename AccT<R>::T e2 = acc1 ? d21 : d2;
+        acc2 = s.lnu[C + c] * Tc < -e2;
         if (acc2) {
           code = acc1 ? 3 : 2;
           s.theta[(k + 1) * C + c] = s.thn[C + c];
         }
-        put_trace(a, c < G.nchains, chain, t + 1, k + 1, acc2, s.thn[C + c], s.lnu[C + c], e2);
+        put_trace(a, c < G.nchains, chain, t + 1, k + 1, acc2, s.thn[C + c], s.lnu[C + c],
+                  (double)e2);
       }
       s.acc[c] += acc1 + acc2;
       s.commit[c] = code;
