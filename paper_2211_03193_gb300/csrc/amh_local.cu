@@ -108,14 +108,16 @@ __device__ __forceinline__ double local_term<double>(const Tab<double>& tb, long
 }
 
 // Delta V_local of a window's pairs on the texture path (FP32): for each
-// downstream atom b, the upstream atoms a in [lo, p) up to kLA at a time with
-// no branch, so a thread keeps 2 kLA fetches in flight (a loop over a waits
+// downstream atom b, the upstream atoms a in [lo, p) up to NA at a time with
+// no branch, so a thread keeps 2 NA fetches in flight (a loop over a waits
 // for each pair's fetches in turn).  Slots past p, and pairs at or past the
 // last bin centre both before and after the move, read nothing and add
 // 0 - 0; the terms are added in the order of the plain loop below, so the
 // sum is the same bit for bit.  cbs: the window's C-betas, [(j*3+xyz)][nt].
-constexpr int kLA = 8;  // windows up to d = 14 (p - lo <= h + 1)
+// NA is the smallest of 3, 5, 8 that holds h + 1 >= p - lo (d up to 14).
+constexpr int kLA = 8;
 
+template <int NA>
 __device__ __forceinline__ float window_pairs_tex(const float* cbs, int nt, int tid, int L,
                                                   int lo, int p, int hi, const Aff<float>& A,
                                                   const Tab<float>& tb, long long tab_off) {
@@ -127,7 +129,7 @@ __device__ __forceinline__ float window_pairs_tex(const float* cbs, int nt, int 
                                    cbs[(jb * 3 + 2) * nt + tid]);
     const V3<float> yb = apply(A, xb);
 #pragma unroll
-    for (int q = 0; q < kLA; ++q) {
+    for (int q = 0; q < NA; ++q) {
       const unsigned ok = q < na;
       const int jq = ok ? q : 0;
       const V3<float> xa = v3<float>(cbs[(jq * 3 + 0) * nt + tid], cbs[(jq * 3 + 1) * nt + tid],
@@ -252,8 +254,13 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
             A = rotation(Pax, Qax, wrap_angle(thn - th));
             bool done = false;
             if constexpr (sizeof(R) == 4) {
-              if (a.tab.tex && p - lo <= kLA) {
-                acc = window_pairs_tex(cbs, nt, tid, L, lo, p, hi, A, a.tab, P.tab_off);
+              if (a.tab.tex && h + 1 <= kLA) {
+                acc = h + 1 <= 3   ? window_pairs_tex<3>(cbs, nt, tid, L, lo, p, hi, A, a.tab,
+                                                         P.tab_off)
+                      : h + 1 <= 5 ? window_pairs_tex<5>(cbs, nt, tid, L, lo, p, hi, A, a.tab,
+                                                         P.tab_off)
+                                   : window_pairs_tex<kLA>(cbs, nt, tid, L, lo, p, hi, A, a.tab,
+                                                           P.tab_off);
                 done = true;
               }
             }
