@@ -122,22 +122,30 @@ __device__ __forceinline__ float window_pairs_tex(const float* cbs, int nt, int 
                                                   int lo, int p, int hi, const Aff<float>& A,
                                                   const Tab<float>& tb, long long tab_off) {
   const int na = p - lo;
+  // the upstream atoms and the entry index of their pairs with b = p, once:
+  // r(a, b + 1) = r(a, b) + 1
+  V3<float> xa[NA];
+  int re[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const int jq = q < na ? q : 0;
+    xa[q] = v3<float>(cbs[(jq * 3 + 0) * nt + tid], cbs[(jq * 3 + 1) * nt + tid],
+                      cbs[(jq * 3 + 2) * nt + tid]);
+    re[q] = (int)tab_off + row_of(L, lo + jq, p) * tb.Bp;
+  }
   float acc = 0.f;
   for (int b = p; b <= hi; ++b) {
     const int jb = b - lo;
     const V3<float> xb = v3<float>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
                                    cbs[(jb * 3 + 2) * nt + tid]);
     const V3<float> yb = apply(A, xb);
+    const int db = (b - p) * tb.Bp;
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
       const unsigned ok = q < na;
-      const int jq = ok ? q : 0;
-      const V3<float> xa = v3<float>(cbs[(jq * 3 + 0) * nt + tid], cbs[(jq * 3 + 1) * nt + tid],
-                                     cbs[(jq * 3 + 2) * nt + tid]);
-      const int re = (int)tab_off + row_of(L, lo + jq, b) * tb.Bp;
-      const float u1 = bin_sat(dist_fast(xa, yb), tb), u0 = bin_sat(dist_fast(xa, xb), tb);
+      const float u1 = bin_sat(dist_fast(xa[q], yb), tb), u0 = bin_sat(dist_fast(xa[q], xb), tb);
       const unsigned need = ok & (fminf(u0, u1) < 1.f);
-      acc += term_tex_if(re, u1, tb, need) - term_tex_if(re, u0, tb, need);
+      acc += term_tex_if(re[q] + db, u1, tb, need) - term_tex_if(re[q] + db, u0, tb, need);
     }
   }
   return acc;
