@@ -10,10 +10,15 @@
 // e(x), e(A1 x), e(A2 x) and e(A21 x) per pair give Delta-E of move 1 and
 // of move 2 after either outcome of move 1, exactly as in sequential
 // order.  The moving side of a proposal is the smaller one (energy is
-// invariant under rigid motion).  No running energy is kept (a decision
-// needs Delta-E only): the coordinates are rebuilt from the torsions in FP64
-// at entry, every resync_every proposals and at each new sweep, and V is
-// recomputed from scratch (FP64 sum) when the call ends.
+// invariant under rigid motion).  In FP32, pairs that stay beyond the last
+// bin centre are dropped by whole chunks before any distance is formed, and
+// a pair whose images all lie at or past it reads no table entry (it adds
+// exactly zero).  The proposals of the rest of a sweep, with the sines and
+// cosines of their rotations, are made ahead by all threads.  No running
+// energy is kept (a decision needs Delta-E only): the coordinates are
+// rebuilt from the torsions in FP64 at entry, every resync_every proposals
+// and at each new sweep, and V is recomputed from scratch (FP64 sum) when
+// the call ends.
 #include "amh_internal.h"
 
 namespace amh {
