@@ -47,6 +47,8 @@ struct amh_ctx {
   int* queue = nullptr;
   int* err = nullptr;
   unsigned long long* pair_count = nullptr;  // global sweeps' straddle terms: [0] formed, [1] read
+  double* tcache = nullptr;  // the global sweeps' rebuild scratch (SweepArgs::tcache)
+  size_t tcache_bytes = 0;
   TraceRec* trace = nullptr;
   long long* trace_count = nullptr;
   // launch configuration
@@ -167,6 +169,7 @@ SweepArgs<R> make_args(amh_ctx* ctx) {
                ctx->Lmax <= kMaxChunks * kPairChunk + 1;
   a.far_cut = (float)(ctx->c0 + (ctx->B - 1) * ctx->w + 0.01);
   a.pair_count = ctx->pair_count;
+  a.tcache = ctx->tcache;
   a.ladder = ctx->ladder_K ? ctx->ladder : nullptr;
   a.ladder_K = ctx->ladder_K;
   return a;
@@ -327,6 +330,17 @@ amh_status configure_global(amh_ctx* ctx, int C, int threads, int D) {
   int per_sm = 1;
   CK(ctx, gocc<R>(C, D > 0, threads, sm, &per_sm));
   ctx->grid_global = std::max(1, std::min(ctx->nggroups, ctx->sm_count * std::max(per_sm, 1)));
+  // the rebuild's scratch: the residue transforms of every chain slot of
+  // every resident CTA (grown here, before any sweep is issued, never inside
+  // a captured stream)
+  const size_t need = (size_t)ctx->grid_global * C * ctx->Lmax * 12 * sizeof(double);
+  if (need > ctx->tcache_bytes) {
+    if (ctx->tcache) cudaFree(ctx->tcache);
+    ctx->tcache = nullptr;
+    ctx->tcache_bytes = 0;
+    CK(ctx, cudaMalloc(&ctx->tcache, need));
+    ctx->tcache_bytes = need;
+  }
   return AMH_OK;
 }
 
@@ -709,7 +723,7 @@ void free_ctx(amh_ctx* ctx) {
   void* ptrs[] = {ctx->table, ctx->theta, ctx->best_theta, ctx->f32buf, ctx->tcount, ctx->E_cur,
                   ctx->best_E, ctx->acc, ctx->prot_d, ctx->chain_prot_d, ctx->ggroups_d,
                   ctx->queue, ctx->err, ctx->trace, ctx->trace_count, ctx->ladder,
-                  ctx->pair_count, ctx->coords, ctx->wgroups_d};
+                  ctx->pair_count, ctx->coords, ctx->wgroups_d, ctx->tcache};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int q = 0; q < 6; ++q)

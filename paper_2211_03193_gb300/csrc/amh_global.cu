@@ -171,9 +171,12 @@ __device__ __forceinline__ V3<R> to_r(V3<double> v) {
 // would carry its whole side off by that angle times the move's angle.  Not
 // inlined: the FP64 scan needs far more registers than the proposal loop,
 // and as a call of its own it no longer sets the whole kernel's allocation
-// (it runs once per sweep; its spills stay inside it).
+// (it runs once per sweep; its spills stay inside it).  cache (global
+// memory, C * L * 12 doubles, or null): the first pass's residue
+// transforms, read back by the second instead of formed again.
 template <class R, int C>
-__device__ __noinline__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L) {
+__device__ __noinline__ void build_chains(Shm<R, C>& s, const Geom<double>& g, int L,
+                                          double* cache) {
   build_chains_scan(
       g, s.kb, L, C, [&](int c, int k) { return (double)s.theta[k * C + c]; },
       [&](int c, int i, V3<double> N, V3<double> CA, V3<double> Cc, V3<double> CB) {
@@ -182,7 +185,7 @@ __device__ __noinline__ void build_chains(Shm<R, C>& s, const Geom<double>& g, i
         s.set_bbv(i, 2, c, to_r<R>(unit(Cc - CA)));
         s.set_cb(i, c, to_r<R>(CB));
       },
-      s.scan);
+      s.scan, cache);
 }
 
 // Reduce three per-lane partial sums over the slices of each chain and
@@ -259,7 +262,8 @@ __device__ void full_energy(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, i
 template <class R, int C>
 __device__ void rebuild(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P) {
   __syncthreads();
-  build_chains(s, a.geom64, P.L);
+  build_chains(s, a.geom64, P.L,
+               a.tcache ? a.tcache + (size_t)blockIdx.x * C * a.Lmax * 12 : nullptr);
   __syncthreads();
 }
 

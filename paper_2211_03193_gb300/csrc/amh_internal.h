@@ -87,6 +87,8 @@ struct SweepArgs {
   long long* trace_count;  // per traced chain, records written
   int* err;
   R* coords;      // per chain C-betas, 3 values per residue at 3 * (torsion offset / 2), or null
+  double* tcache;  // global sweeps: per CTA (blockIdx.x) C * Lmax * 12 doubles where the FP64
+                   // rebuild keeps its residue transforms between its two passes, or null
   int wait_test;  // staged sweeps: > 0 = first wait on an empty ring slot, this many tries
   // a run of whole sweeps with its own T and sigma per sweep (nsched > 0):
   // sweep q of the call (counted from the call's first proposal, which sits
