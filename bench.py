@@ -48,12 +48,12 @@ FLOP_PER_FLAT = 11
 # DRAM bytes of one global-sweep launch from an ncu capture, per launch shape
 # (chains per CTA, threads, staging depth); valid while the kernel's sources
 # hash to sources_sha1.
-TRAFFIC_CAPTURE = {"sources_sha1": "c2af122310efbdf0c945568d84b3e543241f9249",
+TRAFFIC_CAPTURE = {"sources_sha1": "14cbf63e3cd2003ec99ff300ea1509090b7d97e2",
                    "sources": ["paper_2211_03193_gb300/csrc/amh_global.cu",
                                "paper_2211_03193_gb300/csrc/amh_device.cuh",
                                "paper_2211_03193_gb300/csrc/amh_internal.h"],
                    "workload": "amh_L300_c1024",
-                   "bytes": {(1, 1, 128, 0): 16265216}}
+                   "bytes": {(1, 1, 128, 0): 16891136}}
 
 
 def captured_traffic(workload_name, shape):
