@@ -48,7 +48,7 @@ FLOP_PER_FLAT = 11
 # DRAM bytes of one global-sweep launch from an ncu capture, per launch shape
 # (chains per CTA, threads, staging depth); valid while the kernel's sources
 # hash to sources_sha1.
-TRAFFIC_CAPTURE = {"sources_sha1": "14cbf63e3cd2003ec99ff300ea1509090b7d97e2",
+TRAFFIC_CAPTURE = {"sources_sha1": "fa2144c882abdad66e82690a41ef463e56cf9cdf",
                    "sources": ["paper_2211_03193_gb300/csrc/amh_global.cu",
                                "paper_2211_03193_gb300/csrc/amh_device.cuh",
                                "paper_2211_03193_gb300/csrc/amh_internal.h"],

@@ -278,7 +278,8 @@ __device__ void resync(Shm<R, C>& s, const SweepArgs<R>& a, const ProteinDev& P)
 // run are the nlist entries of `list` (item indices mi * nch + ch).  FP32:
 // a pair whose images all lie at or past the last bin centre adds exactly
 // zero (each reads the row's one flat entry), so its entries are not read;
-// nread counts the pairs that were read, for the chain slots set in `real`.
+// nread counts the terms read (4 per pair of a fused proposal pair, 2
+// otherwise), for the chain slots set in `real`.
 template <class R, int C, bool FUSED, bool TEX, bool LIST = false>
 __device__ void pair_block(Shm<R, C>& s, const Tab<R>& tb, long long tab_off, int L, int m0,
                            int m1, int f0, int f1, unsigned real, unsigned& nread,
@@ -805,7 +806,7 @@ __device__ void run_group(Shm<R, C>& s, const SweepArgs<R>& a, const GroupDev& G
   rebuild(s, a, P);
   long long since = 0;
   const unsigned real = G.nchains >= 32 ? ~0u : (1u << G.nchains) - 1u;  // slots holding chains
-  unsigned long long count = 0;  // straddle-pair distances formed (thread 0)
+  unsigned long long count = 0;  // straddle terms whose distances this thread counted as formed
   unsigned nread = 0;            // FP32 terms whose entries this thread read
   long long d0 = 0, dend = 0;  // proposals [d0, dend) have their draws in s.draws
   int kn = (int)(t0 % n);      // torsion index of proposal t0 + j (kept without a 64-bit modulo)
