@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(256) local_kernel(SweepArgs<R> a, int Gc) {
                 done = true;
               }
             }
+            // the plain loop: FP64, table entries through L1, or windows past d = 14
             for (int b = p; b <= hi && !done; ++b) {
               const int jb = b - lo;
               const V3<R> xb = v3<R>(cbs[(jb * 3 + 0) * nt + tid], cbs[(jb * 3 + 1) * nt + tid],
